@@ -1,0 +1,199 @@
+/*
+ * ewh.h -- C ABI of the GB300 El-WaveHoltz library (libewh.so).
+ *
+ * El-WaveHoltz (Appelo, Garcia, Alvarez Loya, Runborg) finds the time-harmonic
+ * solution v of the elastic (Navier) equation rho w^2 v + div T(v) = f
+ * (Section 2.2, eq. elastic-frequency) by applying the WaveHoltz operator
+ *     Pi u0 = (2/T) int_0^T (cos wt - 1/4) u(t) dt,   T = 2 pi / w
+ * (Section 3, eq. el_WHI_OP) inside a Krylov solve of the symmetric positive
+ * definite system M (I - S) v = M Pi 0 (Section 4.5, eq. amat_sym), where
+ * u(t) solves rho u_tt = div T(u) - f cos wt (Section 2.1, eq. elastic-time)
+ * with u(0) = u0, u_t(0) = 0 and S is Pi with f = 0.
+ *
+ * Discretisation (Section 4.1 and 4.3): nodes of a Cartesian grid, an
+ * energy-conserving symmetric L_h (order 2: compact; order 4: fourth-order
+ * summation-by-parts) with diagonal mass M, the time-corrected explicit
+ * leapfrog of eq. (elastic-time-explicit-corrected) with the Taylor start, and
+ * the trapezoidal rule for the filter integral (eq. qoper).
+ *
+ * Conventions shared by every entry point
+ *   - Grid: n[a] nodes along axis a *including* both boundary nodes, spacing h.
+ *   - Sides (bc[6] = x-, x+, y-, y+, z-, z+): EWH_BC_DIRICHLET fixes the
+ *     boundary nodes to zero (they are not unknowns); EWH_BC_FREE makes the side
+ *     traction free (its boundary nodes are unknowns).
+ *   - Media rho, lambda, mu: one double per node of the full grid, C order
+ *     [z][y][x] (x fastest).  Forcing: [nrhs][dim][z][y][x] on the full grid.
+ *   - Solution-space vectors (v_in, v_out, b, x0, ...): double precision,
+ *     [nrhs][dim][z][y][x] over the UNKNOWN nodes only (Dirichlet boundary
+ *     nodes removed), x fastest.  Device pointers unless stated otherwise.
+ *   - Every call returns an ewh_status; nothing throws across the ABI.  A
+ *     failing call leaves a message retrievable with ewh_last_error().
+ *     Asynchronous CUDA errors surface as EWH_ECUDA at the next call.
+ *   - Calls on one context are not thread safe; distinct contexts are
+ *     independent.
+ */
+#ifndef EWH_H
+#define EWH_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ewh_ctx ewh_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  EWH_OK = 0,
+  EWH_EINVAL = 1,      /* invalid argument (sizes, media, omega, ...) */
+  EWH_ENOMEM = 2,      /* device or host allocation failed */
+  EWH_ECUDA = 3,       /* a CUDA call failed */
+  EWH_ENOTCONV = 4,    /* Krylov solve hit maxit before tol */
+  EWH_EBREAKDOWN = 5,  /* CG found (p, (I-S)p)_M <= 0: system not definite */
+  EWH_ETIMEOUT = 6     /* a bounded device-side wait gave up */
+} ewh_status;
+
+enum { EWH_BC_DIRICHLET = 0, EWH_BC_FREE = 1 };
+
+/* Arithmetic of the wave solves.  Krylov vectors, inner products and
+ * residual norms are always FP64. */
+enum {
+  EWH_FP64 = 0,          /* FP64 stencil, state and filter */
+  EWH_FP32_STENCIL = 1   /* FP32 stencil, state and filter; FP64 Krylov.  The
+                            solve refines against FP64 S applies until the FP64
+                            residual meets tol. */
+};
+
+typedef struct {
+  int dim;        /* 2 or 3 */
+  int n[3];       /* nodes per axis including the two boundary nodes (>= 4;
+                     >= 8 for order 4) */
+  double h;       /* grid spacing (> 0) */
+  int order;      /* 2 or 4 */
+  int bc[6];      /* EWH_BC_DIRICHLET or EWH_BC_FREE per side */
+  int precision;  /* EWH_FP64 or EWH_FP32_STENCIL */
+  double cfl;     /* dt_CFL = cfl h / sqrt(max (lambda + (dim+1) mu) / rho);
+                     0 selects 0.5.  Must be in (0, 1). */
+  int periods;    /* K >= 1: filter over K periods (eq. many_periods_filter) */
+  int corrected;  /* 1: time-corrected scheme (Section 4.3, default);
+                     0: standard leapfrog (converges to the w~ problem) */
+  int nt;         /* time steps per period; 0 = ceil(T / dt_CFL), at least 5 */
+} ewh_grid_desc;
+
+/* Scalars of a created problem. */
+typedef struct {
+  int nt;              /* steps per period */
+  int periods;
+  double dt;           /* T / nt */
+  double omega;
+  double omega_tilde;  /* 2 sin(w dt / 2) / dt */
+  double kt;           /* c dt^2, c = (w~/w)^2 if corrected else 1 */
+  long long nodes;     /* unknown nodes per component */
+  long long n_unknowns;/* dim * nodes (one right-hand side) */
+  int nrhs;
+  int nu[3];           /* unknown nodes per axis */
+} ewh_problem_info;
+
+typedef struct {
+  int iters;           /* Krylov iterations (max over right-hand sides) */
+  int s_applies;       /* S applications of the working precision */
+  int s_applies_fp64;  /* FP64 S applications used for residual checks */
+  double rel_res;      /* final ||b - (I-S)x||_M / ||b||_M, max over rhs,
+                          recomputed with an FP64 S apply */
+  double seconds;      /* wall time of the solve (device work included) */
+  int status;          /* ewh_status of the solve */
+} ewh_solve_info;
+
+/* Create a problem (Section 2.1 data, Section 4 discretisation).
+ *   desc       grid, boundary conditions, order, precision, cfl, periods.
+ *   rho,lambda,mu  host or device pointers, one double per full-grid node;
+ *              copied.  Requires rho > 0, mu > 0, lambda > -2 mu / dim, finite.
+ *   omega      angular frequency w > 0 (T = 2 pi / w).
+ *   forcing    host or device pointer [nrhs][dim][full grid] or NULL (f = 0);
+ *              copied.  The wave equation uses -f cos(wt).
+ *   nrhs       >= 1 right-hand sides that share medium and w.
+ *   cuda_stream  the caller's cudaStream_t (NULL = legacy default stream);
+ *              work is ordered after prior work on it, and the stream waits
+ *              for the library's work before each call returns.
+ *   out        receives the context (NULL on failure).
+ * Errors: EWH_EINVAL (bad sizes, media, omega, unstable cfl, order 4 on an
+ * axis with fewer than 8 nodes), EWH_ENOMEM, EWH_ECUDA. */
+ewh_status ewh_create(const ewh_grid_desc* desc, const double* rho, const double* lambda,
+                      const double* mu, double omega, const double* forcing, int nrhs,
+                      void* cuda_stream, ewh_ctx** out);
+
+/* Fill *info with the problem's scalars. */
+ewh_status ewh_get_info(const ewh_ctx* ctx, ewh_problem_info* info);
+
+/* v_out = S v_in (Section 3: Pi with f = 0; eq. qoper): nt*periods leapfrog
+ * steps from u(0) = v_in, u_t(0) = 0 with the trapezoid accumulation.
+ * Device FP64 vectors of nrhs * n_unknowns; v_in and v_out may alias.
+ * Computed in the context's precision. */
+ewh_status ewh_apply_S(ewh_ctx* ctx, const double* v_in, double* v_out);
+
+/* Same as ewh_apply_S but always in FP64, whatever the context precision. */
+ewh_status ewh_apply_S_fp64(ewh_ctx* ctx, const double* v_in, double* v_out);
+
+/* b_out = Pi 0 (eq. amat_non_sym right-hand side): the forced solve from rest.
+ * Device FP64, nrhs * n_unknowns, context precision. */
+ewh_status ewh_apply_Pi0(ewh_ctx* ctx, double* b_out);
+
+/* out = M^{-1} K u = -M^{-1} L_h u (the spatial operator of Section 4.1 alone,
+ * FP64).  Device FP64 vectors of nrhs * n_unknowns. */
+ewh_status ewh_apply_minvK(ewh_ctx* ctx, const double* u, double* out);
+
+/* out[r] = (x_r, y_r)_M, the M inner product per right-hand side (FP64,
+ * deterministic order).  x, y device FP64; out host array of nrhs doubles. */
+ewh_status ewh_mdot(ewh_ctx* ctx, const double* x, const double* y, double* out);
+
+/* Solve M (I - S) v = M Pi 0 (eq. amat_sym) by CG in the M inner product,
+ * independently for every right-hand side.
+ *   tol        stop when ||b - (I-S)x||_M <= tol ||b||_M (b = Pi 0).
+ *   maxit      iteration cap (working-precision CG iterations in total).
+ *   x0_or_null initial guess (FP64, host or device) or NULL for zero.
+ *   v_out      solution (FP64, host or device), nrhs * n_unknowns.
+ *   info       optional; filled on return.
+ * Returns EWH_OK, EWH_ENOTCONV (best iterate in v_out), EWH_EBREAKDOWN
+ * (indefinite system detected; last iterate in v_out), or an error. */
+ewh_status ewh_solve(ewh_ctx* ctx, double tol, int maxit, const double* x0_or_null,
+                     double* v_out, ewh_solve_info* info);
+
+/* Copy up to cap entries of the last solve's residual history (relative
+ * M-norm of the recursive residual after each iteration, max over rhs) to the
+ * host array out; returns the number of entries available via *count. */
+ewh_status ewh_residual_history(const ewh_ctx* ctx, double* out, int cap, int* count);
+
+/* Number of kernel launches the library has issued on this context
+ * (including launches inside graphs), for accounting. */
+long long ewh_kernel_launches(const ewh_ctx* ctx);
+
+/* Device-time accounting of the leapfrog steps.  Every wave solve (S or Pi 0
+ * apply) is bracketed by CUDA events on the context's stream; the elapsed
+ * times are accumulated per precision.  Index 0 = FP64, 1 = FP32. */
+typedef struct {
+  double wave_ms[2];     /* device milliseconds spent in wave solves */
+  long long steps[2];    /* leapfrog steps (time levels) those solves covered */
+  long long waves[2];    /* number of wave solves */
+  long long launches;    /* kernel launches issued (as ewh_kernel_launches) */
+} ewh_stats;
+
+/* Fill *out (synchronises the context's stream first). */
+ewh_status ewh_get_stats(ewh_ctx* ctx, ewh_stats* out);
+
+/* Zero the accumulated statistics (the launch counter included). */
+ewh_status ewh_reset_stats(ewh_ctx* ctx);
+
+/* Release every resource of the context (NULL is ignored). */
+void ewh_destroy(ewh_ctx* ctx);
+
+/* Message of the last failing call on ctx (or of the last failed create when
+ * ctx is NULL).  Never NULL; owned by the library. */
+const char* ewh_last_error(const ewh_ctx* ctx);
+
+/* Static name of a status code. */
+const char* ewh_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EWH_H */

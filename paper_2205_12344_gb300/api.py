@@ -1,0 +1,117 @@
+"""User-facing wrapper over the C ABI.  Device memory comes from PyTorch; every
+step of the computation runs in libewh.so (there is no CPU path: without a
+CUDA device, creating a context raises)."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _lib as L
+
+
+def make_desc(dim, n, h, order, bc, precision=L.EWH_FP64, cfl=0.5, periods=1, corrected=1, nt=0):
+    d = L.ewh_grid_desc()
+    d.dim = int(dim)
+    for a in range(3):
+        d.n[a] = int(n[a]) if a < dim else 1
+    d.h = float(h)
+    d.order = int(order)
+    bc = list(bc) + [0] * (6 - len(bc))
+    for k in range(6):
+        d.bc[k] = int(bc[k])
+    d.precision = int(precision)
+    d.cfl = float(cfl)
+    d.periods = int(periods)
+    d.corrected = int(corrected)
+    d.nt = int(nt)
+    return d
+
+
+PRECISIONS = {"fp64": L.EWH_FP64, "fp32": L.EWH_FP32_STENCIL}
+
+
+class WaveHoltz:
+    """One El-WaveHoltz problem (medium, frequency, forcing) on the current GPU."""
+
+    def __init__(self, prob, precision="fp64", nt=0, stream=None, forcing=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("WaveHoltz needs a CUDA device (libewh.so has no CPU path)")
+        self.torch = torch
+        self.prob = prob
+        self.precision = precision
+        desc = make_desc(prob.dim, prob.n, prob.h, prob.order, prob.bc, PRECISIONS[precision],
+                         prob.cfl, prob.periods, prob.corrected, nt)
+        rho = np.ascontiguousarray(prob.rho, dtype=np.float64)
+        lam = np.ascontiguousarray(prob.lam, dtype=np.float64)
+        mu = np.ascontiguousarray(prob.mu, dtype=np.float64)
+        f = np.ascontiguousarray(prob.forcing, dtype=np.float64) if forcing else None
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        self.ctx = L.ewh_create(desc, rho, lam, mu, prob.omega, f, prob.nrhs, s)
+        self.info = L.ewh_get_info(self.ctx)
+        self.nrhs = prob.nrhs
+        self.n = int(self.info.n_unknowns) * prob.nrhs
+
+    # -- helpers
+    def _vec(self, x=None):
+        t = self.torch
+        if x is None:
+            return t.empty(self.n, dtype=t.float64, device="cuda")
+        if not isinstance(x, t.Tensor):
+            x = t.as_tensor(np.ascontiguousarray(x, dtype=np.float64))
+        return x.to(device="cuda", dtype=t.float64).contiguous().reshape(-1)
+
+    def apply_S(self, v, fp64=False):
+        v = self._vec(v)
+        out = self._vec()
+        (L.ewh_apply_S_fp64 if fp64 else L.ewh_apply_S)(self.ctx, v, out)
+        return out
+
+    def apply_Pi0(self):
+        out = self._vec()
+        L.ewh_apply_Pi0(self.ctx, out)
+        return out
+
+    def apply_minvK(self, u):
+        u = self._vec(u)
+        out = self._vec()
+        L.ewh_apply_minvK(self.ctx, u, out)
+        return out
+
+    def mdot(self, x, y):
+        return L.ewh_mdot(self.ctx, self._vec(x), self._vec(y), self.nrhs)
+
+    def solve(self, tol=1e-8, maxit=100000, x0=None, raise_on_error=True):
+        out = self._vec()
+        x0v = self._vec(x0) if x0 is not None else None
+        info = L.ewh_solve(self.ctx, tol, maxit, x0v, out, raise_on_error=raise_on_error)
+        return out, info
+
+    def residual_history(self):
+        return L.ewh_residual_history(self.ctx)
+
+    def kernel_launches(self):
+        return L.ewh_kernel_launches(self.ctx)
+
+    def stats(self):
+        return L.ewh_get_stats(self.ctx)
+
+    def reset_stats(self):
+        L.ewh_reset_stats(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            self.torch.cuda.synchronize()
+            L.ewh_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,114 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ewh {
+
+// Padding (ghost layers, always zero) around the full node grid of every
+// device field.  Order 4 reads up to 6 nodes beyond a tile; tiles are at most
+// 32 wide and the padded extents are rounded up to a multiple of 32 first.
+constexpr int PAD = 6;
+constexpr int TILE_ROUND = 32;
+
+// Geometry of one problem in the padded device layout.
+struct Geom {
+  int dim;
+  int n[3];        // full-grid nodes per axis (n[2] = 1 in 2D)
+  int lo_free[3];  // 1 if the low side of the axis is a free surface
+  int hi_free[3];
+  int np[3];       // padded extents (np[2] = 1 in 2D)
+  int pz;          // padding along z (PAD in 3D, 0 in 2D)
+  long long plane; // np[0] * np[1]
+  long long field; // elements of one padded component: plane * np[2]
+  int nu[3];       // unknown nodes per axis
+  int off[3];      // full-grid index of the first unknown node per axis
+  long long nodes; // unknown nodes per component
+  int nrhs;
+};
+
+__host__ __device__ inline long long pidx(const Geom& g, int rhs, int comp, int x, int y, int z) {
+  return ((long long)(rhs * g.dim + comp)) * g.field +
+         (long long)(z + g.pz) * g.plane + (long long)(y + PAD) * g.np[0] + (x + PAD);
+}
+
+// 1 if full-grid node (x, y, z) is an unknown.
+__host__ __device__ inline bool is_unknown(const Geom& g, int x, int y, int z) {
+  if (x < 0 || x >= g.n[0] || y < 0 || y >= g.n[1] || z < 0 || z >= g.n[2]) return false;
+  if (x == 0 && !g.lo_free[0]) return false;
+  if (x == g.n[0] - 1 && !g.hi_free[0]) return false;
+  if (y == 0 && !g.lo_free[1]) return false;
+  if (y == g.n[1] - 1 && !g.hi_free[1]) return false;
+  if (g.dim == 3) {
+    if (z == 0 && !g.lo_free[2]) return false;
+    if (z == g.n[2] - 1 && !g.hi_free[2]) return false;
+  }
+  return true;
+}
+
+// Scalars of one time step (host-computed in FP64).
+struct StepScalars {
+  double kt;     // c dt^2
+  double cosn;   // cos(w t_n) of the level whose operator is applied
+  double w0;     // filter weight of u^0 (first step only)
+  double wnew;   // filter weight of the new level
+};
+
+enum StepMode { STEP_FIRST = 0, STEP_MID = 1, STEP_LAST = 2 };
+
+// Pointers of one wave solve (padded fields, all right-hand sides).
+template <typename T>
+struct WaveFields {
+  T* u_cur;        // u^n (halo reads)
+  T* u_next;       // u^{n+1}
+  T* delta;        // u^{n+1} - u^n (in place)
+  T* acc;          // trapezoid accumulator
+  const T* lam;    // medium (shared by the right-hand sides)
+  const T* mu;
+  const T* irh2;   // 1 / (rho h^2)
+  const T* frho;   // f / rho per rhs and component, or nullptr (S apply)
+  T* sigma;        // order-4 stress scratch (dim*(dim+1)/2 fields per rhs) or nullptr
+};
+
+// ---- launchers (ewh_stencil.cu) -------------------------------------------
+template <typename T>
+cudaError_t launch_step(const Geom& g, int order, const WaveFields<T>& f, StepMode mode,
+                        const StepScalars& s, cudaStream_t st, long long* nlaunch);
+template <typename T>
+cudaError_t launch_minvK(const Geom& g, int order, const T* u, T* out, const T* lam,
+                         const T* mu, const T* irh2, T* sigma, cudaStream_t st, long long* nlaunch);
+
+// ---- vector kernels (ewh_krylov.cu) -----------------------------------------
+// dense FP64 [rhs][comp][unknowns] <-> padded T
+template <typename T>
+cudaError_t launch_pack(const Geom& g, const double* dense, T* padded, cudaStream_t st);
+template <typename T>
+cudaError_t launch_unpack(const Geom& g, const T* padded, double* dense, const double* sub_from,
+                          cudaStream_t st);
+// Fused CG direction update and pack: p = r + beta_r p (per rhs), padded = (T) p.
+template <typename T>
+cudaError_t launch_pupdate_pack(const Geom& g, const double* r, double* p, const double* beta,
+                                T* padded, cudaStream_t st);
+
+// Deterministic M inner products: partial sums into part[rhs][nblk], then
+// a fixed-order second pass.
+int dot_blocks(const Geom& g);
+cudaError_t launch_mdot_partial(const Geom& g, const double* mw, const double* x, const double* y,
+                                double* part, cudaStream_t st);
+cudaError_t launch_mdot_final(const Geom& g, const double* part, double* out, cudaStream_t st);
+
+// CG pieces (all scalars per rhs live on the device):
+//   alpha = active ? rr / pq : 0  (sets breakdown flag if pq <= 0)
+cudaError_t launch_cg_alpha(int nrhs, const double* pq_part, int nblk, const double* rr,
+                            double* alpha, int* active, int* flags, cudaStream_t st);
+//   x += alpha p ; r -= alpha q ; partial (r, r)_M
+cudaError_t launch_cg_xr_update(const Geom& g, const double* mw, const double* alpha, const double* p,
+                                const double* q, double* x, double* r, double* part, cudaStream_t st);
+//   rr_new = sum part ; beta = rr_new / rr ; rr = rr_new ; res = sqrt(rr_new / bb)
+cudaError_t launch_cg_beta(int nrhs, const double* part, int nblk, double* rr, const double* bb,
+                           double* beta, double* res, const int* active, cudaStream_t st);
+cudaError_t launch_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t st);
+cudaError_t launch_fill_mass(const Geom& g, int order, const double* rho_full, double h, double* mw,
+                             cudaStream_t st);
+
+}  // namespace ewh

@@ -1,0 +1,293 @@
+// FP64 Krylov kernels for CG in the M inner product (Section 4.5, eq.
+// amat_sym) and the conversions between the solver's dense vectors and the
+// padded wave fields.  Reductions are deterministic: fixed per-thread strides,
+// warp-shuffle and shared-memory trees of fixed shape, and a second pass that
+// adds the per-block partial sums in a fixed order.
+#include <cuda_runtime.h>
+
+#include "ewh_internal.cuh"
+
+namespace ewh {
+
+constexpr int RED_THREADS = 256;
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double warp_part[RED_THREADS / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) warp_part[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (wid == 0) {
+    t = lane < RED_THREADS / 32 ? warp_part[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  __syncthreads();
+  return t;  // valid in thread 0
+}
+
+// dense index -> (comp, node) decomposition helpers
+__device__ __forceinline__ void node_coords(const Geom& g, long long node, int& x, int& y, int& z) {
+  const long long nxy = (long long)g.nu[0] * g.nu[1];
+  z = (int)(node / nxy);
+  const long long r = node - (long long)z * nxy;
+  y = (int)(r / g.nu[0]);
+  x = (int)(r - (long long)y * g.nu[0]);
+  x += g.off[0];
+  y += g.off[1];
+  z += g.off[2];
+}
+
+template <typename T>
+__global__ void pack_kernel(Geom g, const double* __restrict__ dense, T* __restrict__ padded) {
+  const long long total = (long long)g.nrhs * g.dim * g.nodes;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long node = i % g.nodes;
+    const long long rc = i / g.nodes;
+    const int comp = (int)(rc % g.dim), rhs = (int)(rc / g.dim);
+    int x, y, z;
+    node_coords(g, node, x, y, z);
+    padded[pidx(g, rhs, comp, x, y, z)] = (T)dense[i];
+  }
+}
+
+template <typename T>
+__global__ void unpack_kernel(Geom g, const T* __restrict__ padded, double* __restrict__ dense,
+                              const double* __restrict__ sub_from) {
+  const long long total = (long long)g.nrhs * g.dim * g.nodes;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long node = i % g.nodes;
+    const long long rc = i / g.nodes;
+    const int comp = (int)(rc % g.dim), rhs = (int)(rc / g.dim);
+    int x, y, z;
+    node_coords(g, node, x, y, z);
+    const double v = (double)padded[pidx(g, rhs, comp, x, y, z)];
+    dense[i] = sub_from ? sub_from[i] - v : v;
+  }
+}
+
+template <typename T>
+__global__ void pupdate_pack_kernel(Geom g, const double* __restrict__ r, double* __restrict__ p,
+                                    const double* __restrict__ beta, T* __restrict__ padded) {
+  const long long total = (long long)g.nrhs * g.dim * g.nodes;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long node = i % g.nodes;
+    const long long rc = i / g.nodes;
+    const int comp = (int)(rc % g.dim), rhs = (int)(rc / g.dim);
+    const double pn = r[i] + beta[rhs] * p[i];
+    p[i] = pn;
+    int x, y, z;
+    node_coords(g, node, x, y, z);
+    padded[pidx(g, rhs, comp, x, y, z)] = (T)pn;
+  }
+}
+
+static int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+template <typename T>
+cudaError_t launch_pack(const Geom& g, const double* dense, T* padded, cudaStream_t st) {
+  const long long n = (long long)g.nrhs * g.dim * g.nodes;
+  pack_kernel<T><<<grid_for(n), 256, 0, st>>>(g, dense, padded);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_unpack(const Geom& g, const T* padded, double* dense, const double* sub_from,
+                          cudaStream_t st) {
+  const long long n = (long long)g.nrhs * g.dim * g.nodes;
+  unpack_kernel<T><<<grid_for(n), 256, 0, st>>>(g, padded, dense, sub_from);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_pupdate_pack(const Geom& g, const double* r, double* p, const double* beta, T* padded,
+                                cudaStream_t st) {
+  const long long n = (long long)g.nrhs * g.dim * g.nodes;
+  pupdate_pack_kernel<T><<<grid_for(n), 256, 0, st>>>(g, r, p, beta, padded);
+  return cudaGetLastError();
+}
+
+// ---- M inner products ------------------------------------------------------
+int dot_blocks(const Geom& g) {
+  const long long n = (long long)g.dim * g.nodes;
+  long long b = (n + 4 * RED_THREADS - 1) / (4 * RED_THREADS);
+  if (b > 1024) b = 1024;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// partial sums of sum_i mw[node(i)] x_i y_i over one rhs: grid (nblk, nrhs)
+__global__ void mdot_partial_kernel(Geom g, const double* __restrict__ mw, const double* __restrict__ x,
+                                    const double* __restrict__ y, double* __restrict__ part) {
+  const int rhs = blockIdx.y;
+  const long long n = (long long)g.dim * g.nodes;
+  const double* xr = x + (long long)rhs * n;
+  const double* yr = y + (long long)rhs * n;
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)RED_THREADS + threadIdx.x; i < n;
+       i += (long long)gridDim.x * RED_THREADS)
+    s += mw[i % g.nodes] * xr[i] * yr[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[(long long)rhs * gridDim.x + blockIdx.x] = s;
+}
+
+__device__ double sum_partials(const double* part, int nblk) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += RED_THREADS) s += part[i];
+  return block_sum(s);
+}
+
+__global__ void mdot_final_kernel(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+  const int rhs = blockIdx.x;
+  const double s = sum_partials(part + (long long)rhs * nblk, nblk);
+  if (threadIdx.x == 0) out[rhs] = s;
+}
+
+cudaError_t launch_mdot_partial(const Geom& g, const double* mw, const double* x, const double* y, double* part,
+                                cudaStream_t st) {
+  dim3 grd(dot_blocks(g), g.nrhs);
+  mdot_partial_kernel<<<grd, RED_THREADS, 0, st>>>(g, mw, x, y, part);
+  return cudaGetLastError();
+}
+cudaError_t launch_mdot_final(const Geom& g, const double* part, double* out, cudaStream_t st) {
+  mdot_final_kernel<<<g.nrhs, RED_THREADS, 0, st>>>(part, dot_blocks(g), out);
+  return cudaGetLastError();
+}
+
+// ---- CG scalar kernels -----------------------------------------------------
+// flags bit 0: breakdown (pq <= 0 on an active rhs)
+__global__ void cg_alpha_kernel(const double* __restrict__ pq_part, int nblk, const double* __restrict__ rr,
+                                double* __restrict__ alpha, int* __restrict__ active, int* __restrict__ flags) {
+  const int rhs = blockIdx.x;
+  const double pq = sum_partials(pq_part + (long long)rhs * nblk, nblk);
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    if (active[rhs]) {
+      if (pq > 0.0 && isfinite(pq)) {
+        a = rr[rhs] / pq;
+      } else {
+        atomicOr(flags, 1);
+        active[rhs] = 0;
+      }
+    }
+    alpha[rhs] = a;
+  }
+}
+
+__global__ void cg_xr_kernel(Geom g, const double* __restrict__ mw, const double* __restrict__ alpha,
+                             const double* __restrict__ p, const double* __restrict__ q, double* __restrict__ x,
+                             double* __restrict__ r, double* __restrict__ part) {
+  const int rhs = blockIdx.y;
+  const long long n = (long long)g.dim * g.nodes;
+  const long long base = (long long)rhs * n;
+  const double a = alpha[rhs];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)RED_THREADS + threadIdx.x; i < n;
+       i += (long long)gridDim.x * RED_THREADS) {
+    const long long k = base + i;
+    x[k] += a * p[k];
+    const double rn = r[k] - a * q[k];
+    r[k] = rn;
+    s += mw[i % g.nodes] * rn * rn;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[(long long)rhs * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void cg_beta_kernel(const double* __restrict__ part, int nblk, double* __restrict__ rr,
+                               const double* __restrict__ bb, double* __restrict__ beta, double* __restrict__ res,
+                               const int* __restrict__ active) {
+  const int rhs = blockIdx.x;
+  const double rn = sum_partials(part + (long long)rhs * nblk, nblk);
+  if (threadIdx.x == 0) {
+    if (active[rhs]) {
+      beta[rhs] = rr[rhs] > 0.0 ? rn / rr[rhs] : 0.0;
+      rr[rhs] = rn;
+      res[rhs] = sqrt(rn / bb[rhs]);
+    } else {
+      beta[rhs] = 0.0;
+    }
+  }
+}
+
+cudaError_t launch_cg_alpha(int nrhs, const double* pq_part, int nblk, const double* rr, double* alpha, int* active,
+                            int* flags, cudaStream_t st) {
+  cg_alpha_kernel<<<nrhs, RED_THREADS, 0, st>>>(pq_part, nblk, rr, alpha, active, flags);
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_xr_update(const Geom& g, const double* mw, const double* alpha, const double* p, const double* q,
+                                double* x, double* r, double* part, cudaStream_t st) {
+  dim3 grd(dot_blocks(g), g.nrhs);
+  cg_xr_kernel<<<grd, RED_THREADS, 0, st>>>(g, mw, alpha, p, q, x, r, part);
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_beta(int nrhs, const double* part, int nblk, double* rr, const double* bb, double* beta,
+                           double* res, const int* active, cudaStream_t st) {
+  cg_beta_kernel<<<nrhs, RED_THREADS, 0, st>>>(part, nblk, rr, bb, beta, res, active);
+  return cudaGetLastError();
+}
+
+__global__ void axpby_kernel(long long n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+cudaError_t launch_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t st) {
+  axpby_kernel<<<grid_for(n), 256, 0, st>>>(n, a, x, b, y);
+  return cudaGetLastError();
+}
+
+// ---- mass weights: rho * (trapezoid or SBP norm product) * h^dim per unknown node
+__device__ __forceinline__ double axis_weight(int p, int N, int lo_free, int hi_free, int order) {
+  if (order == 4) {
+    const int q = p < N - 1 - p ? p : N - 1 - p;
+    switch (q) {
+      case 0: return 17.0 / 48.0;
+      case 1: return 59.0 / 48.0;
+      case 2: return 43.0 / 48.0;
+      case 3: return 49.0 / 48.0;
+      default: return 1.0;
+    }
+  }
+  if ((p == 0 && lo_free) || (p == N - 1 && hi_free)) return 0.5;
+  return 1.0;
+}
+
+__global__ void fill_mass_kernel(Geom g, int order, const double* __restrict__ rho_full, double hd,
+                                 double* __restrict__ mw) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.nodes;
+       i += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    node_coords(g, i, x, y, z);
+    double w = axis_weight(x, g.n[0], g.lo_free[0], g.hi_free[0], order) *
+               axis_weight(y, g.n[1], g.lo_free[1], g.hi_free[1], order);
+    if (g.dim == 3) w *= axis_weight(z, g.n[2], g.lo_free[2], g.hi_free[2], order);
+    const long long full = ((long long)z * g.n[1] + y) * g.n[0] + x;
+    mw[i] = rho_full[full] * w * hd;
+  }
+}
+cudaError_t launch_fill_mass(const Geom& g, int order, const double* rho_full, double h, double* mw,
+                             cudaStream_t st) {
+  double hd = h * h;
+  if (g.dim == 3) hd *= h;
+  fill_mass_kernel<<<grid_for(g.nodes), 256, 0, st>>>(g, order, rho_full, hd, mw);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_pack<float>(const Geom&, const double*, float*, cudaStream_t);
+template cudaError_t launch_pack<double>(const Geom&, const double*, double*, cudaStream_t);
+template cudaError_t launch_unpack<float>(const Geom&, const float*, double*, const double*, cudaStream_t);
+template cudaError_t launch_unpack<double>(const Geom&, const double*, double*, const double*, cudaStream_t);
+template cudaError_t launch_pupdate_pack<float>(const Geom&, const double*, double*, const double*, float*,
+                                                cudaStream_t);
+template cudaError_t launch_pupdate_pack<double>(const Geom&, const double*, double*, const double*, double*,
+                                                 cudaStream_t);
+
+}  // namespace ewh

@@ -1,0 +1,435 @@
+// Fused leapfrog + trapezoid-filter step kernels.
+//
+// One launch advances every right-hand side by one time level of the
+// time-corrected explicit scheme (Section 4.3, eq. elastic-time-explicit-
+// corrected), written in increment form
+//     delta^{n+1} = delta^n - kt (M^{-1} K u^n + (f / rho) cos(w t_n)),
+//     u^{n+1}     = u^n + delta^{n+1},
+//     acc        += w_{n+1} u^{n+1}                (trapezoid filter, eq. qoper)
+// with the Taylor start folded into the first launch:
+//     delta^1 = -(kt/2) (M^{-1} K u^0 + f / rho),  acc = w_0 u^0 + w_1 u^1.
+// K = -L_h is the Hessian of the discrete elastic energy (Section 4.1):
+//   order 2: compact form; pure terms on edges with edge coefficients equal
+//            to the mean of the two end nodes, mixed terms at nodes with
+//            centred differences (one-sided on a free boundary node), the
+//            trapezoid factor 1/2 per free side;
+//   order 4: pointwise energy density with all first derivatives from the
+//            fourth-order diagonal-norm summation-by-parts operator D; then
+//            M^{-1} K u = (1/(rho h^2)) sum_a [ -D_a sigma_{.a} + H_a^{-1} B_a sigma_{.a} ].
+#include <cuda_runtime.h>
+
+#include "ewh_internal.cuh"
+
+namespace ewh {
+
+// Boundary closure of the diagonal-norm 2-4 SBP first derivative (rows 0..3,
+// columns 0..5); the last four rows are the negated mirror.  Norm weight of
+// the boundary row: 17/48.
+__constant__ double c_sbp_d[4][6] = {
+    {-24.0 / 17, 59.0 / 34, -4.0 / 17, -3.0 / 34, 0.0, 0.0},
+    {-0.5, 0.0, 0.5, 0.0, 0.0, 0.0},
+    {4.0 / 43, -59.0 / 86, 0.0, 59.0 / 86, -4.0 / 43, 0.0},
+    {3.0 / 98, 0.0, -59.0 / 98, 0.0, 32.0 / 49, -4.0 / 49}};
+__constant__ float c_sbp_f[4][6] = {
+    {-24.0f / 17, 59.0f / 34, -4.0f / 17, -3.0f / 34, 0.0f, 0.0f},
+    {-0.5f, 0.0f, 0.5f, 0.0f, 0.0f, 0.0f},
+    {4.0f / 43, -59.0f / 86, 0.0f, 59.0f / 86, -4.0f / 43, 0.0f},
+    {3.0f / 98, 0.0f, -59.0f / 98, 0.0f, 32.0f / 49, -4.0f / 49}};
+
+template <typename T>
+__device__ __forceinline__ T sbp_coef(int r, int j);
+template <>
+__device__ __forceinline__ double sbp_coef<double>(int r, int j) { return c_sbp_d[r][j]; }
+template <>
+__device__ __forceinline__ float sbp_coef<float>(int r, int j) { return c_sbp_f[r][j]; }
+
+// SBP first derivative along one axis at position p of a line of N nodes;
+// v points at the node, s is the element stride along the axis.
+template <typename T>
+__device__ __forceinline__ T sbp_d1(const T* v, long long s, int p, int N) {
+  if (p < 4) {
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) acc += sbp_coef<T>(p, j) * v[(long long)(j - p) * s];
+    return acc;
+  }
+  if (p > N - 5) {
+    const int r = N - 1 - p;
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) acc -= sbp_coef<T>(r, j) * v[(long long)(r - j) * s];
+    return acc;
+  }
+  return (v[-2 * s] - T(8) * v[-s] + T(8) * v[s] - v[2 * s]) * T(1.0 / 12.0);
+}
+
+// ---------------------------------------------------------------------------
+// Time update shared by all kernels.  a = M^{-1} K u (FP of the state).
+// ---------------------------------------------------------------------------
+template <typename T, int MODE, bool FORCED>
+__device__ __forceinline__ void leapfrog_update(const WaveFields<T>& f, long long p, T uval, T a,
+                                                const StepScalars& s) {
+  if (MODE == 3) {  // operator only
+    f.u_next[p] = a;
+    return;
+  }
+  if (FORCED) a += f.frho[p] * T(s.cosn);
+  if (MODE == STEP_FIRST) {
+    const T d = T(-0.5) * T(s.kt) * a;
+    const T un = uval + d;
+    f.delta[p] = d;
+    f.u_next[p] = un;
+    f.acc[p] = T(s.w0) * uval + T(s.wnew) * un;
+  } else {
+    const T d = f.delta[p] - T(s.kt) * a;
+    const T un = uval + d;
+    if (MODE == STEP_MID) {
+      f.delta[p] = d;
+      f.u_next[p] = un;
+    }
+    f.acc[p] += T(s.wnew) * un;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Order 2, 2D: 32 x 8 tile, one node per thread, halo 1 in shared memory.
+// ---------------------------------------------------------------------------
+template <typename T, int MODE, bool FORCED>
+__global__ void __launch_bounds__(256) step2d_o2(Geom g, WaveFields<T> f, StepScalars s) {
+  constexpr int TX = 32, TY = 8, SX = TX + 2, SY = TY + 2;
+  __shared__ T su[2][SY][SX];
+  __shared__ T sl[SY][SX];
+  __shared__ T sm[SY][SX];
+  const int rhs = blockIdx.z;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  for (int i = tid; i < SX * SY; i += TX * TY) {
+    const int lx = i % SX, ly = i / SX;
+    const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+    const long long pu = pidx(g, rhs, 0, gx, gy, 0);
+    su[0][ly][lx] = f.u_cur[pu];
+    su[1][ly][lx] = f.u_cur[pu + g.field];
+    const long long pc = pidx(g, 0, 0, gx, gy, 0);
+    sl[ly][lx] = f.lam[pc];
+    sm[ly][lx] = f.mu[pc];
+  }
+  __syncthreads();
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  if (!is_unknown(g, x, y, 0)) return;
+  const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
+  const int nx = g.n[0], ny = g.n[1];
+  // at an unknown node, sitting on the first/last grid line means a free side
+  const bool fxl = (x == 0), fxh = (x == nx - 1), fyl = (y == 0), fyh = (y == ny - 1);
+
+  auto U = [&](int c, int dx, int dy) -> T { return su[c][ty + dy][tx + dx]; };
+  auto L = [&](int dx, int dy) -> T { return sl[ty + dy][tx + dx]; };
+  auto M = [&](int dx, int dy) -> T { return sm[ty + dy][tx + dx]; };
+  auto coef = [&](bool p_wave, int dx, int dy) -> T {
+    return p_wave ? L(dx, dy) + T(2) * M(dx, dy) : M(dx, dy);
+  };
+  // pure terms (edges), already divided by the trapezoid factor of the node
+  auto pureX = [&](int c, bool p_wave) -> T {
+    const T c0 = coef(p_wave, 0, 0);
+    T t = T(0);
+    if (x > 0) t += T(0.5) * (c0 + coef(p_wave, -1, 0)) * (U(c, 0, 0) - U(c, -1, 0));
+    if (x < nx - 1) t -= T(0.5) * (c0 + coef(p_wave, 1, 0)) * (U(c, 1, 0) - U(c, 0, 0));
+    return (fxl || fxh) ? T(2) * t : t;
+  };
+  auto pureY = [&](int c, bool p_wave) -> T {
+    const T c0 = coef(p_wave, 0, 0);
+    T t = T(0);
+    if (y > 0) t += T(0.5) * (c0 + coef(p_wave, 0, -1)) * (U(c, 0, 0) - U(c, 0, -1));
+    if (y < ny - 1) t -= T(0.5) * (c0 + coef(p_wave, 0, 1)) * (U(c, 0, 1) - U(c, 0, 0));
+    return (fyl || fyh) ? T(2) * t : t;
+  };
+  // centred differences at the node offset by dx (resp. dy)
+  auto CyAt = [&](int c, int dx) -> T {
+    if (fyh) return U(c, dx, 0) - U(c, dx, -1);
+    if (fyl) return U(c, dx, 1) - U(c, dx, 0);
+    return T(0.5) * (U(c, dx, 1) - U(c, dx, -1));
+  };
+  auto CxAt = [&](int c, int dy) -> T {
+    if (fxh) return U(c, 0, dy) - U(c, -1, dy);
+    if (fxl) return U(c, 1, dy) - U(c, 0, dy);
+    return T(0.5) * (U(c, 1, dy) - U(c, -1, dy));
+  };
+  // transposed centred difference (divided by the node's trapezoid factor)
+  auto Gx = [&](bool use_lam, int c, int dx) -> T {
+    if (!is_unknown(g, x + dx, y, 0)) return T(0);
+    return (use_lam ? L(dx, 0) : M(dx, 0)) * CyAt(c, dx);
+  };
+  auto Gy = [&](bool use_lam, int c, int dy) -> T {
+    if (!is_unknown(g, x, y + dy, 0)) return T(0);
+    return (use_lam ? L(0, dy) : M(0, dy)) * CxAt(c, dy);
+  };
+  auto Zx = [&](bool use_lam, int c) -> T {
+    if (fxh) return Gx(use_lam, c, -1) + Gx(use_lam, c, 0);
+    if (fxl) return -(Gx(use_lam, c, 0) + Gx(use_lam, c, 1));
+    return T(0.5) * (Gx(use_lam, c, -1) - Gx(use_lam, c, 1));
+  };
+  auto Zy = [&](bool use_lam, int c) -> T {
+    if (fyh) return Gy(use_lam, c, -1) + Gy(use_lam, c, 0);
+    if (fyl) return -(Gy(use_lam, c, 0) + Gy(use_lam, c, 1));
+    return T(0.5) * (Gy(use_lam, c, -1) - Gy(use_lam, c, 1));
+  };
+  // K u for u (x-displacement) and v (y-displacement)
+  const T Ku = pureX(0, true) + pureY(0, false) + Zx(true, 1) + Zy(false, 1);
+  const T Kv = pureX(1, false) + pureY(1, true) + Zy(true, 0) + Zx(false, 0);
+  const T irh = f.irh2[pidx(g, 0, 0, x, y, 0)];
+  const long long p0 = pidx(g, rhs, 0, x, y, 0);
+  leapfrog_update<T, MODE, FORCED>(f, p0, U(0, 0, 0), Ku * irh, s);
+  leapfrog_update<T, MODE, FORCED>(f, p0 + g.field, U(1, 0, 0), Kv * irh, s);
+}
+
+// ---------------------------------------------------------------------------
+// Order 2, 3D: 32 x 4 x 2 tile, halo 1.
+// ---------------------------------------------------------------------------
+template <typename T, int MODE, bool FORCED>
+__global__ void __launch_bounds__(256) step3d_o2(Geom g, WaveFields<T> f, StepScalars s) {
+  constexpr int TX = 32, TY = 4, TZ = 2, SX = TX + 2, SY = TY + 2, SZ = TZ + 2;
+  __shared__ T su[3][SZ][SY][SX];
+  __shared__ T sl[SZ][SY][SX];
+  __shared__ T sm[SZ][SY][SX];
+  const int nzb = (g.n[2] + TZ - 1) / TZ;
+  const int rhs = blockIdx.z / nzb;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = (blockIdx.z % nzb) * TZ;
+  const int tid = (threadIdx.z * TY + threadIdx.y) * TX + threadIdx.x;
+  for (int i = tid; i < SX * SY * SZ; i += TX * TY * TZ) {
+    const int lx = i % SX, ly = (i / SX) % SY, lz = i / (SX * SY);
+    const int gx = x0 - 1 + lx, gy = y0 - 1 + ly, gz = z0 - 1 + lz;
+    const long long pu = pidx(g, rhs, 0, gx, gy, gz);
+    su[0][lz][ly][lx] = f.u_cur[pu];
+    su[1][lz][ly][lx] = f.u_cur[pu + g.field];
+    su[2][lz][ly][lx] = f.u_cur[pu + 2 * g.field];
+    const long long pc = pidx(g, 0, 0, gx, gy, gz);
+    sl[lz][ly][lx] = f.lam[pc];
+    sm[lz][ly][lx] = f.mu[pc];
+  }
+  __syncthreads();
+  const int pos[3] = {x0 + (int)threadIdx.x, y0 + (int)threadIdx.y, z0 + (int)threadIdx.z};
+  if (!is_unknown(g, pos[0], pos[1], pos[2])) return;
+  const int t0[3] = {(int)threadIdx.x + 1, (int)threadIdx.y + 1, (int)threadIdx.z + 1};
+  const bool lo[3] = {pos[0] == 0, pos[1] == 0, pos[2] == 0};
+  const bool hi[3] = {pos[0] == g.n[0] - 1, pos[1] == g.n[1] - 1, pos[2] == g.n[2] - 1};
+
+  auto U = [&](int c, int dx, int dy, int dz) -> T { return su[c][t0[2] + dz][t0[1] + dy][t0[0] + dx]; };
+  auto L = [&](int dx, int dy, int dz) -> T { return sl[t0[2] + dz][t0[1] + dy][t0[0] + dx]; };
+  auto Mu = [&](int dx, int dy, int dz) -> T { return sm[t0[2] + dz][t0[1] + dy][t0[0] + dx]; };
+  auto Uo = [&](int c, const int* o) -> T { return U(c, o[0], o[1], o[2]); };
+
+  T Kc[3];
+#pragma unroll
+  for (int al = 0; al < 3; ++al) {
+    T acc = T(0);
+    // pure terms along every axis
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int e[3] = {0, 0, 0};
+      e[a] = 1;
+      const T c0 = (al == a) ? L(0, 0, 0) + T(2) * Mu(0, 0, 0) : Mu(0, 0, 0);
+      T t = T(0);
+      if (pos[a] > 0) {
+        const T cl = (al == a) ? L(-e[0], -e[1], -e[2]) + T(2) * Mu(-e[0], -e[1], -e[2]) : Mu(-e[0], -e[1], -e[2]);
+        t += T(0.5) * (c0 + cl) * (U(al, 0, 0, 0) - U(al, -e[0], -e[1], -e[2]));
+      }
+      if (pos[a] < g.n[a] - 1) {
+        const T cr = (al == a) ? L(e[0], e[1], e[2]) + T(2) * Mu(e[0], e[1], e[2]) : Mu(e[0], e[1], e[2]);
+        t -= T(0.5) * (c0 + cr) * (U(al, e[0], e[1], e[2]) - U(al, 0, 0, 0));
+      }
+      acc += (lo[a] || hi[a]) ? T(2) * t : t;
+    }
+    // mixed terms: for each beta != alpha
+    //   Z_alpha( lambda C_beta u_beta ) + Z_beta( mu C_alpha u_beta )
+#pragma unroll
+    for (int be = 0; be < 3; ++be) {
+      if (be == al) continue;
+#pragma unroll
+      for (int term = 0; term < 2; ++term) {
+        const int za = term == 0 ? al : be;   // axis of the transposed difference
+        const int cb = term == 0 ? be : al;   // axis of the inner difference
+        auto G = [&](int k) -> T {
+          int o[3] = {0, 0, 0};
+          o[za] = k;
+          if (!is_unknown(g, pos[0] + o[0], pos[1] + o[1], pos[2] + o[2])) return T(0);
+          int op[3] = {o[0], o[1], o[2]}, om[3] = {o[0], o[1], o[2]};
+          op[cb] += 1;
+          om[cb] -= 1;
+          T d;
+          if (hi[cb]) d = Uo(be, o) - Uo(be, om);
+          else if (lo[cb]) d = Uo(be, op) - Uo(be, o);
+          else d = T(0.5) * (Uo(be, op) - Uo(be, om));
+          const T cf = term == 0 ? L(o[0], o[1], o[2]) : Mu(o[0], o[1], o[2]);
+          return cf * d;
+        };
+        T z;
+        if (hi[za]) z = G(-1) + G(0);
+        else if (lo[za]) z = -(G(0) + G(1));
+        else z = T(0.5) * (G(-1) - G(1));
+        acc += z;
+      }
+    }
+    Kc[al] = acc;
+  }
+  const T irh = f.irh2[pidx(g, 0, 0, pos[0], pos[1], pos[2])];
+  const long long p0 = pidx(g, rhs, 0, pos[0], pos[1], pos[2]);
+#pragma unroll
+  for (int al = 0; al < 3; ++al)
+    leapfrog_update<T, MODE, FORCED>(f, p0 + al * g.field, U(al, 0, 0, 0), Kc[al] * irh, s);
+}
+
+// ---------------------------------------------------------------------------
+// Order 4 (SBP), any dimension: stress pass then divergence + update pass.
+// Stress fields per rhs: 2D (xx, yy, xy); 3D (xx, yy, zz, xy, xz, yz).
+// ---------------------------------------------------------------------------
+template <int DIM>
+__host__ __device__ constexpr int nsig() { return DIM == 2 ? 3 : 6; }
+template <int DIM>
+__device__ __forceinline__ int sig_index(int a, int b) {
+  if (a == b) return a;
+  if (DIM == 2) return 2;
+  const int lo = a < b ? a : b, hi = a < b ? b : a;
+  return lo == 0 ? (hi == 1 ? 3 : 4) : 5;
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) sbp_stress(Geom g, const T* __restrict__ u, const T* __restrict__ lam,
+                                                  const T* __restrict__ mu, T* __restrict__ sig) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  int z = 0, rhs = blockIdx.z;
+  if (DIM == 3) {
+    const int nz = g.n[2];
+    z = blockIdx.z % nz;
+    rhs = blockIdx.z / nz;
+  }
+  if (x >= g.n[0] || y >= g.n[1]) return;
+  const int pos[3] = {x, y, z};
+  const long long stride[3] = {1, (long long)g.np[0], g.plane};
+  // gradient grad[alpha][a] = D_a u_alpha
+  T grad[DIM][DIM];
+#pragma unroll
+  for (int al = 0; al < DIM; ++al) {
+    const T* base = u + pidx(g, rhs, al, x, y, z);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) grad[al][a] = sbp_d1<T>(base, stride[a], pos[a], g.n[a]);
+  }
+  const long long pc = pidx(g, 0, 0, x, y, z);
+  const T l = lam[pc], m = mu[pc];
+  T div = T(0);
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) div += grad[a][a];
+  T* out = sig + (long long)rhs * nsig<DIM>() * g.field + (pc - 0);
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) out[(long long)a * g.field] = l * div + T(2) * m * grad[a][a];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a)
+#pragma unroll
+    for (int b = a + 1; b < DIM; ++b)
+      out[(long long)sig_index<DIM>(a, b) * g.field] = m * (grad[a][b] + grad[b][a]);
+}
+
+template <typename T, int DIM, int MODE, bool FORCED>
+__global__ void __launch_bounds__(256) sbp_divergence_step(Geom g, WaveFields<T> f, StepScalars s) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  int z = 0, rhs = blockIdx.z;
+  if (DIM == 3) {
+    const int nz = g.n[2];
+    z = blockIdx.z % nz;
+    rhs = blockIdx.z / nz;
+  }
+  if (!is_unknown(g, x, y, z)) return;
+  const int pos[3] = {x, y, z};
+  const long long stride[3] = {1, (long long)g.np[0], g.plane};
+  const long long pc = pidx(g, 0, 0, x, y, z);
+  const T* sig = f.sigma + (long long)rhs * nsig<DIM>() * g.field + pc;
+  const T inv_h0 = T(48.0 / 17.0);
+  const T irh = f.irh2[pc];
+  const long long p0 = pidx(g, rhs, 0, x, y, z);
+#pragma unroll
+  for (int al = 0; al < DIM; ++al) {
+    T k = T(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const T* sa = sig + (long long)sig_index<DIM>(al, a) * g.field;
+      k -= sbp_d1<T>(sa, stride[a], pos[a], g.n[a]);
+      if (pos[a] == 0) k -= inv_h0 * sa[0];                 // free low side
+      else if (pos[a] == g.n[a] - 1) k += inv_h0 * sa[0];   // free high side
+    }
+    const long long p = p0 + al * g.field;
+    leapfrog_update<T, MODE, FORCED>(f, p, f.u_cur[p], k * irh, s);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <typename T, int MODE, bool FORCED>
+static cudaError_t launch_mode(const Geom& g, int order, const WaveFields<T>& f, const StepScalars& s,
+                               cudaStream_t st, long long* nl) {
+  if (order == 2) {
+    if (g.dim == 2) {
+      dim3 blk(32, 8), grd((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.nrhs);
+      step2d_o2<T, MODE, FORCED><<<grd, blk, 0, st>>>(g, f, s);
+    } else {
+      dim3 blk(32, 4, 2), grd((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, ((g.n[2] + 1) / 2) * g.nrhs);
+      step3d_o2<T, MODE, FORCED><<<grd, blk, 0, st>>>(g, f, s);
+    }
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+  }
+  dim3 blk(32, 8);
+  dim3 grd((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.dim == 2 ? g.nrhs : g.n[2] * g.nrhs);
+  if (g.dim == 2) {
+    sbp_stress<T, 2><<<grd, blk, 0, st>>>(g, f.u_cur, f.lam, f.mu, f.sigma);
+    sbp_divergence_step<T, 2, MODE, FORCED><<<grd, blk, 0, st>>>(g, f, s);
+  } else {
+    sbp_stress<T, 3><<<grd, blk, 0, st>>>(g, f.u_cur, f.lam, f.mu, f.sigma);
+    sbp_divergence_step<T, 3, MODE, FORCED><<<grd, blk, 0, st>>>(g, f, s);
+  }
+  if (nl) *nl += 2;
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_step(const Geom& g, int order, const WaveFields<T>& f, StepMode mode,
+                        const StepScalars& s, cudaStream_t st, long long* nl) {
+  const bool forced = f.frho != nullptr;
+  switch (mode) {
+    case STEP_FIRST:
+      return forced ? launch_mode<T, STEP_FIRST, true>(g, order, f, s, st, nl)
+                    : launch_mode<T, STEP_FIRST, false>(g, order, f, s, st, nl);
+    case STEP_MID:
+      return forced ? launch_mode<T, STEP_MID, true>(g, order, f, s, st, nl)
+                    : launch_mode<T, STEP_MID, false>(g, order, f, s, st, nl);
+    default:
+      return forced ? launch_mode<T, STEP_LAST, true>(g, order, f, s, st, nl)
+                    : launch_mode<T, STEP_LAST, false>(g, order, f, s, st, nl);
+  }
+}
+
+template <typename T>
+cudaError_t launch_minvK(const Geom& g, int order, const T* u, T* out, const T* lam, const T* mu,
+                         const T* irh2, T* sigma, cudaStream_t st, long long* nl) {
+  WaveFields<T> f{};
+  f.u_cur = const_cast<T*>(u);
+  f.u_next = out;
+  f.lam = lam;
+  f.mu = mu;
+  f.irh2 = irh2;
+  f.frho = nullptr;
+  f.sigma = sigma;
+  StepScalars s{};
+  return launch_mode<T, 3, false>(g, order, f, s, st, nl);
+}
+
+template cudaError_t launch_step<float>(const Geom&, int, const WaveFields<float>&, StepMode,
+                                        const StepScalars&, cudaStream_t, long long*);
+template cudaError_t launch_step<double>(const Geom&, int, const WaveFields<double>&, StepMode,
+                                         const StepScalars&, cudaStream_t, long long*);
+template cudaError_t launch_minvK<float>(const Geom&, int, const float*, float*, const float*, const float*,
+                                         const float*, float*, cudaStream_t, long long*);
+template cudaError_t launch_minvK<double>(const Geom&, int, const double*, double*, const double*,
+                                          const double*, const double*, double*, cudaStream_t, long long*);
+
+}  // namespace ewh

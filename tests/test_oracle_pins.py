@@ -486,3 +486,21 @@ def test_windowed_S_equals_full_S_at_centre():
         a = full[c * nn + idx[cy, cx]]
         b = outw[c * wnn + widx[cy - lo[1], cx - lo[0]]]
         assert abs(a - b) <= 1e-12 * np.abs(full).max()
+
+
+def test_window_helper_matches_full_apply():
+    """The domain-of-dependence helper used by the full-size GPU parity tests
+    reproduces the full-domain oracle S v at nodes by a free top corner and by
+    a Dirichlet corner (order 4: stencil reach 4)."""
+    from _helpers import window_sample
+    p = inputs.cfg_layered_2d(nu=70, order=4)
+    p.omega *= 4.0                                # few steps -> small windows
+    s = O.build_system(p)
+    v = inputs.random_vectors(p, 1, 31)[0]
+    full = O.apply_S(s, v)
+    idx = inputs.unknown_index(p)
+    nn = p.n_nodes()
+    for node in [(6, p.n[1] - 2), (p.n[0] - 3, 4)]:
+        got = window_sample(p, s.nt, v, node, reach=4)
+        want = np.array([full[c * nn + idx[node[1], node[0]]] for c in range(2)])
+        assert np.abs(got - want).max() <= 1e-12 * np.abs(full).max()
