@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the El-WaveHoltz hot path on GB300.
+
+Workload: the 2D layered seismic medium (1024 x 1024 unknowns + free top row,
+h = 10 m, 8 layers, Vp 1.5-4.5 km/s, Vs = Vp/sqrt(3), rho 1.8-2.6 g/cc,
+traction-free top, Dirichlet elsewhere, w for 10 points per shear wavelength,
+Ricker source), fourth-order SBP stencil, FP32 stencil with FP64 Krylov.
+
+One step = one pass of the whole hot path from a cold start: Pi 0 (forced FP64
+wave solve), then ITERS iterations of CG in the M inner product on the FP32
+operator (each one FP32 S apply = nt leapfrog levels with the trapezoid
+filter, plus the FP64 Krylov updates), FP64 true-residual replacements, and
+the final FP64 residual.  A complete solve of this workload to 1e-6 needs
+tens of thousands of iterations (cond(I - S) ~ w^(2d)), far beyond a bench
+step, so the time-to-1e-6 comparison against the plain FP64 GPU solve is
+measured on smaller layered media of the same family (and on the 64 x 64
+homogeneous case), solved to tolerance by both.
+
+value = grid-point updates (nodes x leapfrog levels over every wave solve of
+the step, FP32 and FP64) per second, whole job.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 launch with torch.distributed.run; every rank solves its own shot
+(weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gpt-updates/s, HBM % of peak; time to 1e-6 residual vs plain FP64 GPU solve"
+UNIT = "Gpt-updates/s"
+ALG_BYTES_2D_FP32 = 52.0      # bytes per grid-point update of one unfused leapfrog+filter pass
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nu", type=int, default=1024)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--iters", type=int, default=100, help="CG iterations per step")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the plain FP64 GPU solve used for the time-to-tol comparison")
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(nu, rank, world):
+    from paper_2205_12344_gb300 import inputs
+    # each rank's shot sits at its own horizontal position (independent problems)
+    L = (nu + 1) * 0.01
+    shot = L * (rank + 1) / (world + 1)
+    return inputs.cfg_layered_2d(nu=nu, order=4, shot_x=[shot])
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("ewh_stencil.cu", "ewh_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2205_12344_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_step(nodes):
+    """DRAM bytes per leapfrog step of the dominant kernels from the committed
+    ncu summary, scaled to ``nodes``; None when absent or stale."""
+    p = os.path.join(ROOT, "profiles", "step_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_node_step"]) * nodes
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        loaded = sorted(sm)[len(sm) // 4:] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_sample(prob, nt, window_nodes=512, min_seconds=8.0):
+    """Time the FP64 oracle's S apply on a bounded window of the workload
+    (domain-of-dependence crop; single host thread).  Returns (Gpt/s, desc)."""
+    import numpy as np
+    from oracle import ewh_oracle as O
+    from paper_2205_12344_gb300 import inputs
+    cx = prob.n[0] // 2
+    half = window_nodes // 2
+    lo = [cx - half, prob.n[1] - window_nodes]
+    hi = [cx + half - 1, prob.n[1] - 1]
+    w = inputs.window_problem(prob, lo, hi)
+    s = O.build_system(w, nt=nt)
+    v = np.random.default_rng(0).standard_normal(s.K.shape[0])
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        O.apply_S(s, v)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    upd = reps * w.n_nodes() * nt
+    return upd / el / 1e9, {"window": "%dx%d nodes by the free top" % (window_nodes, window_nodes),
+                            "s_applies": reps, "seconds": round(el, 2)}
+
+
+def time_to_tol_table(flush, stream):
+    """Time to a relative FP64 residual of 1e-6 (1e-8 for the homogeneous case)
+    for the plain FP64 GPU solve and the FP32-stencil / FP64-Krylov solve, each
+    timed with CUDA events after one untimed warm solve."""
+    import torch
+    from paper_2205_12344_gb300 import inputs
+    from paper_2205_12344_gb300.api import WaveHoltz
+    cases = [("homogeneous2d_64 (64x64, order 2, w=10)", inputs.cfg_homogeneous_2d(nu=64, omega=10.0), 1e-8),
+             ("layered2d_256 (256x256 + free top, order 4, 10 PPW)", inputs.cfg_layered_2d(nu=256, order=4), 1e-6)]
+    out = []
+    for name, prob, tol in cases:
+        row = {"workload": name, "tol": tol}
+        sols = {}
+        for prec in ("fp64", "fp32"):
+            wh = WaveHoltz(prob, precision=prec)
+            wh.solve(tol=tol, maxit=200000, raise_on_error=False)
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x, info = wh.solve(tol=tol, maxit=200000, raise_on_error=False)
+            e1.record(stream)
+            e1.synchronize()
+            sols[prec] = x
+            row[prec] = {"seconds": e0.elapsed_time(e1) / 1e3, "iters": info.iters, "rel_res": info.rel_res,
+                         "status": info.status, "s_applies_fp32": info.s_applies,
+                         "s_applies_fp64": info.s_applies_fp64}
+            wh.close()
+        row["speedup_mixed_vs_fp64"] = row["fp64"]["seconds"] / row["fp32"]["seconds"]
+        row["solution_rel_diff"] = float(torch.linalg.norm(sols["fp32"] - sols["fp64"]) /
+                                         torch.linalg.norm(sols["fp64"]))
+        out.append(row)
+    return out
+
+
+def run_reference(args, ws, rank):
+    """--impl reference: the FP64 CPU oracle as it stands, on host cores."""
+    if rank != 0:
+        return
+    from paper_2205_12344_gb300 import inputs
+    from oracle import ewh_oracle as O
+    prob = workload(args.nu, 0, 1)
+    dtc = O.cfl_dt(2, 4, prob.h, prob.cfl, prob.rho, prob.lam, prob.mu)
+    nt = max(5, int(math.ceil(2 * math.pi / prob.omega / dtc)))
+    for _ in range(args.warmup):
+        cpu_oracle_sample(prob, nt, window_nodes=128, min_seconds=0.5)
+    vals = []
+    descs = []
+    for _ in range(args.steps):
+        v, d = cpu_oracle_sample(prob, nt, window_nodes=256, min_seconds=5.0)
+        vals.append(v)
+        descs.append(d)
+    value = statistics.mean(vals)
+    ms = statistics.mean(d["seconds"] / d["s_applies"] for d in descs) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "layered2d_%d order-4 S apply (oracle sample)" % args.nu,
+                       "nt": nt, "l2": "oracle runs on the host"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "S apply on a 256x256-node window of the workload, nt=%d levels" % nt},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_info()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    from paper_2205_12344_gb300 import build
+    build.build()
+    from paper_2205_12344_gb300 import _lib as L
+    from paper_2205_12344_gb300.api import WaveHoltz
+
+    prob = workload(args.nu, rank, ws)
+    wh = WaveHoltz(prob, precision="fp32")
+    nodes = int(wh.info.nodes)
+    nt = int(wh.info.nt)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def one_solve():
+        return wh.solve(tol=args.tol, maxit=args.iters, raise_on_error=False)
+
+    for _ in range(args.warmup):
+        one_solve()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    wh.reset_stats()
+    clock = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clock:
+        clock.start()
+    step_ms = []
+    infos = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)                      # L2 flush between timed steps (untimed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, info = one_solve()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        infos.append(info)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clock.stop() if clock else None
+    st = wh.stats()
+    total_ms = sum(step_ms)
+    updates = (st.steps[0] + st.steps[1]) * nodes
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        u = torch.tensor([float(updates)], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(u)
+        updates = float(u.item())
+    value = updates / (total_ms * 1e-3) / 1e9
+    # dominant kernel: the FP32 leapfrog step (stress + divergence/update launches)
+    step_dev_ms = st.wave_ms[1] / max(st.steps[1], 1)
+    peak, peak_kind = peaks()
+    achieved = ALG_BYTES_2D_FP32 * nodes / (step_dev_ms * 1e-3) / 1e9
+    traffic = traffic_per_step(nodes)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": peak_kind,
+                "kernel": "FP32 leapfrog step (sbp_stress + sbp_divergence_step), per time level",
+                "alg_bytes_per_node_step": ALG_BYTES_2D_FP32,
+                "fp64_step_ms": (st.wave_ms[0] / st.steps[0]) if st.steps[0] else None}
+    launches = int(st.launches)
+    it = [i.iters for i in infos]
+
+    extra = {}
+    if rank == 0:
+        extra["iters_per_step"] = args.iters
+        extra["rel_res_after_step"] = max(i.rel_res for i in infos)
+        extra["s_applies_fp32_per_step"] = infos[-1].s_applies
+        extra["s_applies_fp64_per_step"] = infos[-1].s_applies_fp64
+        if not args.no_fp64_compare:
+            extra["time_to_tol"] = time_to_tol_table(flush, stream)
+    wh.close()
+
+    # end to end through the C ABI with host buffers: create (H2D of medium and
+    # forcing from pinned memory) + solve (D2H of the solution into host memory)
+    e2e = None
+    if rank == 0:
+        pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(prob, k), dtype=np.float64)).pin_memory()
+               for k in ("rho", "lam", "mu", "forcing")}
+        out_host = torch.empty(prob.nrhs * prob.n_unknowns(), dtype=torch.float64).pin_memory()
+        desc_args = dict(dim=prob.dim, n=prob.n, h=prob.h, order=prob.order, bc=prob.bc,
+                         precision=L.EWH_FP32_STENCIL, cfl=prob.cfl, periods=prob.periods,
+                         corrected=prob.corrected)
+        from paper_2205_12344_gb300.api import make_desc
+        e2e_ms = []
+        e2e_updates = 0
+        for k in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx = L.ewh_create(make_desc(**desc_args), pin["rho"], pin["lam"], pin["mu"], prob.omega,
+                               pin["forcing"], prob.nrhs, stream.cuda_stream)
+            info = L.ewh_solve(ctx, args.tol, args.iters, None, out_host, raise_on_error=False)
+            sts = L.ewh_get_stats(ctx)
+            L.ewh_destroy(ctx)
+            t1 = time.perf_counter()
+            if k > 0:
+                e2e_ms.append((t1 - t0) * 1e3)
+                e2e_updates += (sts.steps[0] + sts.steps[1]) * nodes
+        h2d = sum(int(pin[k].numel()) * 8 for k in pin)
+        d2h = int(out_host.numel()) * 8
+        e2e = {"value": e2e_updates / (sum(e2e_ms) * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": statistics.mean(e2e_ms)}
+
+    if rank == 0:
+        cpu_val, cpu_desc = cpu_oracle_sample(prob, nt) if ws == 1 else (None, None)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 stencil / f64 krylov", "data": "synthetic",
+            "config": {"workload": "layered2d_%d: 2D layered medium %dx%d unknowns + free top row, order-4 SBP, "
+                                   "FP32 stencil + FP64 CG, %d iterations per step" % (args.nu, args.nu, args.nu,
+                                                                                      args.iters),
+                       "nodes": nodes, "nt": nt, "omega": prob.omega, "tol": args.tol,
+                       "parallelism": "independent shots per GPU" if ws > 1 else "single GPU",
+                       "l2": "flushed (256 MiB write) between timed steps"},
+            "roofline": roofline,
+            "cpu_baseline": ({"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                              "sample": "oracle FP64 S apply, %s, %d applies in %.1f s" %
+                                        (cpu_desc["window"], cpu_desc["s_applies"], cpu_desc["seconds"])}
+                             if cpu_val is not None else None),
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        line.update(extra)
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -60,8 +60,10 @@ enum { EWH_BC_DIRICHLET = 0, EWH_BC_FREE = 1 };
 enum {
   EWH_FP64 = 0,          /* FP64 stencil, state and filter */
   EWH_FP32_STENCIL = 1   /* FP32 stencil, state and filter; FP64 Krylov.  The
-                            solve refines against FP64 S applies until the FP64
-                            residual meets tol. */
+                            solve replaces the recursive residual by the FP64
+                            true residual each time it has fallen tenfold, stops
+                            on the FP64 residual, and continues with the FP64
+                            operator if the FP32 one loses definiteness. */
 };
 
 typedef struct {

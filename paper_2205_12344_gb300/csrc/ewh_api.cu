@@ -339,84 +339,6 @@ ewh_status mdot_dev(ewh_ctx* ctx, const double* x, const double* y, double* out_
   return EWH_OK;
 }
 
-// CG on (I - S_T) d = r0 where x holds the iterate and r the residual on entry.
-// Stops when sqrt(rr)/sqrt(bref) <= tol for every rhs (bref in S_BB).
-template <typename T>
-ewh_status run_cg(ewh_ctx* ctx, double* x, double* r, double tol, int maxit, int* iters, int* s_applies,
-                  bool* converged) {
-  const Geom& g = ctx->g;
-  const int R = g.nrhs;
-  const long long n = total_unknowns(ctx);
-  Wave<T>& w = wave_of<T>(ctx);
-  ewh_status st = ensure_graph<T>(ctx, false);
-  if (st != EWH_OK) return st;
-  // rr = (r, r)_M ; p = 0 ; beta = 0 ; active = 1
-  st = mdot_dev(ctx, r, r, sc(ctx, S_RR));
-  if (st != EWH_OK) return st;
-  EWH_CU(cudaMemsetAsync(ctx->kp, 0, sizeof(double) * n, ctx->st));
-  EWH_CU(cudaMemsetAsync(sc(ctx, S_BETA), 0, sizeof(double) * R, ctx->st));
-  EWH_CU(cudaMemsetAsync(ctx->flags, 0, sizeof(int), ctx->st));
-  EWH_CU(cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * S_N * R, cudaMemcpyDeviceToHost, ctx->st));
-  EWH_CU(cudaStreamSynchronize(ctx->st));
-  std::vector<int> act(R, 1);
-  double worst = 0.0;
-  for (int k = 0; k < R; ++k) {
-    const double res = std::sqrt(ctx->h_scal[S_RR * R + k] / ctx->h_scal[S_BB * R + k]);
-    if (res <= tol) act[k] = 0;
-    worst = std::max(worst, res);
-  }
-  EWH_CU(cudaMemcpyAsync(ctx->active, act.data(), sizeof(int) * R, cudaMemcpyHostToDevice, ctx->st));
-  ctx->history.push_back(worst);
-  *converged = (worst <= tol);
-  int it = 0;
-  while (!*converged && it < maxit) {
-    // p = r + beta p ; u^0 = p
-    EWH_CU(launch_pupdate_pack<T>(g, r, ctx->kp, sc(ctx, S_BETA), w.u_a, ctx->st));
-    ctx->launches += 1;
-    EWH_CU(launch_timed_graph<T>(ctx, w.graph_S));
-    ctx->launches += w.graph_S_kernels;
-    // q = p - S p
-    EWH_CU(launch_unpack<T>(g, w.acc, ctx->kq, ctx->kp, ctx->st));
-    EWH_CU(launch_mdot_partial(g, ctx->mw, ctx->kp, ctx->kq, ctx->part, ctx->st));
-    EWH_CU(launch_cg_alpha(R, ctx->part, ctx->nblk, sc(ctx, S_RR), sc(ctx, S_ALPHA), ctx->active, ctx->flags,
-                           ctx->st));
-    EWH_CU(launch_cg_xr_update(g, ctx->mw, sc(ctx, S_ALPHA), ctx->kp, ctx->kq, x, r, ctx->part, ctx->st));
-    EWH_CU(launch_cg_beta(R, ctx->part, ctx->nblk, sc(ctx, S_RR), sc(ctx, S_BB), sc(ctx, S_BETA),
-                          sc(ctx, S_RES), ctx->active, ctx->st));
-    ctx->launches += 5;
-    ++it;
-    ++*s_applies;
-    EWH_CU(cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * S_N * R, cudaMemcpyDeviceToHost, ctx->st));
-    int flag = 0;
-    EWH_CU(cudaMemcpyAsync(&act[0], ctx->active, sizeof(int) * R, cudaMemcpyDeviceToHost, ctx->st));
-    EWH_CU(cudaMemcpyAsync(&flag, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-    EWH_CU(cudaStreamSynchronize(ctx->st));
-    if (flag & 1) {
-      *iters += it;
-      return fail(ctx, EWH_EBREAKDOWN, "CG breakdown: (p, (I-S)p)_M <= 0 (indefinite system near resonance)");
-    }
-    worst = 0.0;
-    bool changed = false;
-    for (int k = 0; k < R; ++k) {
-      const double res = ctx->h_scal[S_RES * R + k];
-      if (act[k] && res <= tol) {
-        act[k] = 0;
-        changed = true;
-      }
-      if (act[k]) worst = std::max(worst, res);
-    }
-    if (changed) EWH_CU(cudaMemcpyAsync(ctx->active, act.data(), sizeof(int) * R, cudaMemcpyHostToDevice, ctx->st));
-    double hist = 0.0;
-    for (int k = 0; k < R; ++k) hist = std::max(hist, ctx->h_scal[S_RES * R + k]);
-    ctx->history.push_back(hist);
-    bool any = false;
-    for (int k = 0; k < R; ++k) any = any || act[k];
-    *converged = !any;
-  }
-  *iters += it;
-  return EWH_OK;
-}
-
 // r = b - (x - S64 x) in FP64, returns per-rhs relative residual (max) on host
 ewh_status true_residual(ewh_ctx* ctx, const double* x, double* r, double* max_rel) {
   const Geom& g = ctx->g;
@@ -436,6 +358,113 @@ ewh_status true_residual(ewh_ctx* ctx, const double* x, double* r, double* max_r
   for (int k = 0; k < R; ++k)
     worst = std::max(worst, std::sqrt(ctx->h_scal[S_DOT * R + k] / ctx->h_scal[S_BB * R + k]));
   *max_rel = worst;
+  return EWH_OK;
+}
+
+// CG in the M inner product on (I - S_T) x = b, S_T the wave solve in
+// precision T.  On entry x holds the iterate and r its true FP64 residual.
+// Residual replacement (van der Vorst and Ye, "Residual replacement strategies
+// for Krylov subspace iterative methods", 2000): whenever the recursive
+// residual of an active rhs has dropped by the factor `drop` since the last
+// replacement, or reaches tol, r is replaced by the true residual b - A64 x
+// (FP64 S apply) while the search direction is kept.  Convergence is declared
+// on the true residual only.  drop = 0 replaces only at convergence.
+template <typename T>
+ewh_status run_cg(ewh_ctx* ctx, double* x, double* r, double tol, int maxit, double drop, ewh_solve_info* inf,
+                  double* rel_out) {
+  const Geom& g = ctx->g;
+  const int R = g.nrhs;
+  const long long n = total_unknowns(ctx);
+  Wave<T>& w = wave_of<T>(ctx);
+  ewh_status st = ensure_graph<T>(ctx, false);
+  if (st != EWH_OK) return st;
+  // rr = (r, r)_M ; p = 0 ; beta = 0
+  st = mdot_dev(ctx, r, r, sc(ctx, S_RR));
+  if (st != EWH_OK) return st;
+  EWH_CU(cudaMemsetAsync(ctx->kp, 0, sizeof(double) * n, ctx->st));
+  EWH_CU(cudaMemsetAsync(sc(ctx, S_BETA), 0, sizeof(double) * R, ctx->st));
+  EWH_CU(cudaMemsetAsync(ctx->flags, 0, sizeof(int), ctx->st));
+  EWH_CU(cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * S_N * R, cudaMemcpyDeviceToHost, ctx->st));
+  EWH_CU(cudaStreamSynchronize(ctx->st));
+  std::vector<int> act(R, 1);
+  std::vector<double> anchor(R), true_res(R);
+  for (int k = 0; k < R; ++k) {
+    true_res[k] = std::sqrt(ctx->h_scal[S_RR * R + k] / ctx->h_scal[S_BB * R + k]);
+    anchor[k] = true_res[k];
+    if (true_res[k] <= tol) act[k] = 0;
+  }
+  EWH_CU(cudaMemcpyAsync(ctx->active, act.data(), sizeof(int) * R, cudaMemcpyHostToDevice, ctx->st));
+  auto worst_true = [&]() {
+    double m = 0.0;
+    for (int k = 0; k < R; ++k) m = std::max(m, true_res[k]);
+    return m;
+  };
+  ctx->history.push_back(worst_true());
+  bool any = false;
+  for (int k = 0; k < R; ++k) any = any || act[k];
+  int it = 0;
+  while (any && inf->iters < maxit) {
+    // p = r + beta p ; u^0 = p
+    EWH_CU(launch_pupdate_pack<T>(g, r, ctx->kp, sc(ctx, S_BETA), w.u_a, ctx->st));
+    ctx->launches += 1;
+    EWH_CU(launch_timed_graph<T>(ctx, w.graph_S));
+    ctx->launches += w.graph_S_kernels;
+    // q = p - S p
+    EWH_CU(launch_unpack<T>(g, w.acc, ctx->kq, ctx->kp, ctx->st));
+    EWH_CU(launch_mdot_partial(g, ctx->mw, ctx->kp, ctx->kq, ctx->part, ctx->st));
+    EWH_CU(launch_cg_alpha(R, ctx->part, ctx->nblk, sc(ctx, S_RR), sc(ctx, S_ALPHA), ctx->active, ctx->flags,
+                           ctx->st));
+    EWH_CU(launch_cg_xr_update(g, ctx->mw, sc(ctx, S_ALPHA), ctx->kp, ctx->kq, x, r, ctx->part, ctx->st));
+    EWH_CU(launch_cg_beta(R, ctx->part, ctx->nblk, sc(ctx, S_RR), sc(ctx, S_BB), sc(ctx, S_BETA),
+                          sc(ctx, S_RES), ctx->active, ctx->st));
+    ctx->launches += 5;
+    ++it;
+    ++inf->iters;
+    if (sizeof(T) == 8) ++inf->s_applies_fp64;
+    else ++inf->s_applies;
+    int flag = 0;
+    EWH_CU(cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * S_N * R, cudaMemcpyDeviceToHost, ctx->st));
+    EWH_CU(cudaMemcpyAsync(act.data(), ctx->active, sizeof(int) * R, cudaMemcpyDeviceToHost, ctx->st));
+    EWH_CU(cudaMemcpyAsync(&flag, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    EWH_CU(cudaStreamSynchronize(ctx->st));
+    if (flag & 1) {
+      *rel_out = worst_true();
+      return fail(ctx, EWH_EBREAKDOWN, "CG breakdown: (p, (I-S)p)_M <= 0 (indefinite system near resonance)");
+    }
+    bool replace = false;
+    double hist = 0.0;
+    for (int k = 0; k < R; ++k) {
+      const double res = ctx->h_scal[S_RES * R + k];
+      if (act[k]) {
+        hist = std::max(hist, res);
+        if (res <= tol || (drop > 0.0 && res <= drop * anchor[k])) replace = true;
+      }
+    }
+    ctx->history.push_back(hist);
+    if (replace) {
+      double dummy = 0.0;
+      st = true_residual(ctx, x, r, &dummy);
+      if (st != EWH_OK) return st;
+      ++inf->s_applies_fp64;
+      EWH_CU(launch_cg_replace(R, sc(ctx, S_DOT), sc(ctx, S_RR), sc(ctx, S_BETA), sc(ctx, S_RES), sc(ctx, S_BB),
+                               ctx->st));
+      ctx->launches += 1;
+      bool changed = false;
+      for (int k = 0; k < R; ++k) {
+        true_res[k] = std::sqrt(ctx->h_scal[S_DOT * R + k] / ctx->h_scal[S_BB * R + k]);
+        anchor[k] = true_res[k];
+        if (act[k] && true_res[k] <= tol) {
+          act[k] = 0;
+          changed = true;
+        }
+      }
+      if (changed) EWH_CU(cudaMemcpyAsync(ctx->active, act.data(), sizeof(int) * R, cudaMemcpyHostToDevice, ctx->st));
+    }
+    any = false;
+    for (int k = 0; k < R; ++k) any = any || act[k];
+  }
+  *rel_out = worst_true();
+  (void)it;
   return EWH_OK;
 }
 
@@ -462,39 +491,26 @@ ewh_status solve_impl(ewh_ctx* ctx, double tol, int maxit, const double* x0, dou
     EWH_CU(cudaMemsetAsync(ctx->kx, 0, sizeof(double) * n, ctx->st));
     EWH_CU(cudaMemcpyAsync(ctx->kr, ctx->kb, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->st));
   }
-  ewh_status result = EWH_OK;
-  bool converged = false;
+  // FP64: replacement only to confirm convergence.  FP32 stencil: replace
+  // every time the recursive residual fell tenfold, so the FP32 operator's
+  // rounding never accumulates in the residual beyond one decade.
+  ewh_status result;
   if (ctx->precision == EWH_FP64) {
-    result = run_cg<double>(ctx, ctx->kx, ctx->kr, tol, maxit, &inf->iters, &inf->s_applies_fp64, &converged);
+    result = run_cg<double>(ctx, ctx->kx, ctx->kr, tol, maxit, 0.0, inf, &rel);
   } else {
-    // FP32 stencil, FP64 Krylov: CG on the FP32 operator for the correction,
-    // refined against FP64 residuals until the FP64 residual meets tol.
-    for (int outer = 0; outer < 12; ++outer) {
-      if (rel <= tol) {
-        converged = true;
-        break;
-      }
-      if (inf->iters >= maxit) break;
-      EWH_CU(cudaMemsetAsync(ctx->kd, 0, sizeof(double) * n, ctx->st));
-      bool inner_conv = false;
-      result = run_cg<float>(ctx, ctx->kd, ctx->kr, 0.5 * tol, maxit - inf->iters, &inf->iters, &inf->s_applies,
-                             &inner_conv);
-      if (result != EWH_OK) break;
-      EWH_CU(launch_axpby(n, 1.0, ctx->kd, 1.0, ctx->kx, ctx->st));
-      ctx->launches += 1;
+    result = run_cg<float>(ctx, ctx->kx, ctx->kr, tol, maxit, 0.1, inf, &rel);
+    if (result == EWH_EBREAKDOWN) {
+      // The FP32 operator lost definiteness on the modes nearest resonance
+      // (its rounding exceeds their eigenvalues of I - S): continue with the
+      // FP64 operator from the current iterate and its true residual.
       s = true_residual(ctx, ctx->kx, ctx->kr, &rel);
       if (s != EWH_OK) return s;
-      inf->s_applies_fp64 += 1;
+      ++inf->s_applies_fp64;
+      ctx->err = "no error";
+      result = run_cg<double>(ctx, ctx->kx, ctx->kr, tol, maxit, 0.0, inf, &rel);
     }
-    converged = rel <= tol;
   }
   if (result != EWH_OK && result != EWH_EBREAKDOWN) return result;
-  // final residual recomputed with an FP64 S apply
-  if (ctx->precision == EWH_FP64 || result == EWH_EBREAKDOWN) {
-    s = true_residual(ctx, ctx->kx, ctx->kq, &rel);
-    if (s != EWH_OK) return s;
-    inf->s_applies_fp64 += 1;
-  }
   inf->rel_res = rel;
   EWH_CU(cudaMemcpyAsync(v_out, ctx->kx, sizeof(double) * n, cudaMemcpyDefault, ctx->st));
   EWH_CU(cudaStreamSynchronize(ctx->st));
@@ -503,7 +519,6 @@ ewh_status solve_impl(ewh_ctx* ctx, double tol, int maxit, const double* x0, dou
     return fail(ctx, EWH_ENOTCONV, "not converged: relative residual " + std::to_string(rel) + " > tol after " +
                                        std::to_string(inf->iters) + " iterations");
   }
-  (void)converged;
   return EWH_OK;
 }
 

@@ -107,6 +107,9 @@ cudaError_t launch_cg_xr_update(const Geom& g, const double* mw, const double* a
 //   rr_new = sum part ; beta = rr_new / rr ; rr = rr_new ; res = sqrt(rr_new / bb)
 cudaError_t launch_cg_beta(int nrhs, const double* part, int nblk, double* rr, const double* bb,
                            double* beta, double* res, const int* active, cudaStream_t st);
+//   after a residual replacement: beta *= dot / rr ; rr = dot ; res = sqrt(dot / bb)
+cudaError_t launch_cg_replace(int nrhs, const double* dot, double* rr, double* beta, double* res, const double* bb,
+                              cudaStream_t st);
 cudaError_t launch_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t st);
 cudaError_t launch_fill_mass(const Geom& g, int order, const double* rho_full, double h, double* mw,
                              cudaStream_t st);

@@ -218,6 +218,22 @@ __global__ void cg_beta_kernel(const double* __restrict__ part, int nblk, double
   }
 }
 
+// residual replacement: the recursive residual was overwritten by the true
+// one with (r, r)_M = dot; rescale beta and reset rr accordingly
+__global__ void cg_replace_kernel(int nrhs, const double* __restrict__ dot, double* __restrict__ rr,
+                                  double* __restrict__ beta, double* __restrict__ res, const double* __restrict__ bb) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nrhs) return;
+  beta[k] = rr[k] > 0.0 ? beta[k] * (dot[k] / rr[k]) : 0.0;
+  rr[k] = dot[k];
+  res[k] = sqrt(dot[k] / bb[k]);
+}
+cudaError_t launch_cg_replace(int nrhs, const double* dot, double* rr, double* beta, double* res, const double* bb,
+                              cudaStream_t st) {
+  cg_replace_kernel<<<(nrhs + 127) / 128, 128, 0, st>>>(nrhs, dot, rr, beta, res, bb);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cg_alpha(int nrhs, const double* pq_part, int nblk, const double* rr, double* alpha, int* active,
                             int* flags, cudaStream_t st) {
   cg_alpha_kernel<<<nrhs, RED_THREADS, 0, st>>>(pq_part, nblk, rr, alpha, active, flags);

@@ -18,6 +18,8 @@
 //            M^{-1} K u = (1/(rho h^2)) sum_a [ -D_a sigma_{.a} + H_a^{-1} B_a sigma_{.a} ].
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+
 #include "ewh_internal.cuh"
 
 namespace ewh {
@@ -96,6 +98,7 @@ __device__ __forceinline__ void leapfrog_update(const WaveFields<T>& f, long lon
 // ---------------------------------------------------------------------------
 template <typename T, int MODE, bool FORCED>
 __global__ void __launch_bounds__(256) step2d_o2(Geom g, WaveFields<T> f, StepScalars s) {
+  if (g.dim != 2) return;
   constexpr int TX = 32, TY = 8, SX = TX + 2, SY = TY + 2;
   __shared__ T su[2][SY][SX];
   __shared__ T sl[SY][SX];
@@ -186,6 +189,7 @@ __global__ void __launch_bounds__(256) step2d_o2(Geom g, WaveFields<T> f, StepSc
 // ---------------------------------------------------------------------------
 template <typename T, int MODE, bool FORCED>
 __global__ void __launch_bounds__(256) step3d_o2(Geom g, WaveFields<T> f, StepScalars s) {
+  if (g.dim != 3) return;
   constexpr int TX = 32, TY = 4, TZ = 2, SX = TX + 2, SY = TY + 2, SZ = TZ + 2;
   __shared__ T su[3][SZ][SY][SX];
   __shared__ T sl[SZ][SY][SX];
@@ -294,6 +298,7 @@ __device__ __forceinline__ int sig_index(int a, int b) {
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) sbp_stress(Geom g, const T* __restrict__ u, const T* __restrict__ lam,
                                                   const T* __restrict__ mu, T* __restrict__ sig) {
+  if (g.dim != DIM) return;  // launched for the wrong dimension: touch nothing
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   int z = 0, rhs = blockIdx.z;
@@ -330,6 +335,7 @@ __global__ void __launch_bounds__(256) sbp_stress(Geom g, const T* __restrict__ 
 
 template <typename T, int DIM, int MODE, bool FORCED>
 __global__ void __launch_bounds__(256) sbp_divergence_step(Geom g, WaveFields<T> f, StepScalars s) {
+  if (g.dim != DIM) return;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   int z = 0, rhs = blockIdx.z;
@@ -362,8 +368,234 @@ __global__ void __launch_bounds__(256) sbp_divergence_step(Geom g, WaveFields<T>
 }
 
 // ---------------------------------------------------------------------------
+// Order 4 (SBP), 2D, fused: one launch per time level.  A 32 x 16 tile (32 x 8
+// in FP64, to stay within 48 KB of static shared memory) stages
+// u on tile +- 6 nodes and lambda, mu on tile +- 3 in shared memory, forms the
+// stresses on tile +- 3 (the closure rows reach 3 nodes), then the divergence
+// and the leapfrog/filter update of its own nodes.
+// ---------------------------------------------------------------------------
+template <typename T>
+__host__ __device__ constexpr int o4_tile_y() { return sizeof(T) == 8 ? 8 : 16; }
+
+template <typename T, int MODE, bool FORCED>
+__global__ void __launch_bounds__(512) step2d_o4_fused(Geom g, WaveFields<T> f, StepScalars s) {
+  if (g.dim != 2) return;
+  constexpr int TX = 32, TY = o4_tile_y<T>(), HU = 6, HS = 3;
+  constexpr int UX = TX + 2 * HU, UY = TY + 2 * HU;
+  constexpr int SX = TX + 2 * HS, SY = TY + 2 * HS;
+  __shared__ T su[2][UY][UX];
+  __shared__ T sl[SY][SX];
+  __shared__ T sm[SY][SX];
+  __shared__ T ss[3][SY][SX];  // xx, yy, xy
+  const int rhs = blockIdx.z;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  const int nx = g.n[0], ny = g.n[1];
+  for (int i = tid; i < UX * UY; i += TX * TY) {
+    const int lx = i % UX, ly = i / UX;
+    const long long pu = pidx(g, rhs, 0, x0 - HU + lx, y0 - HU + ly, 0);
+    su[0][ly][lx] = f.u_cur[pu];
+    su[1][ly][lx] = f.u_cur[pu + g.field];
+  }
+  for (int i = tid; i < SX * SY; i += TX * TY) {
+    const int lx = i % SX, ly = i / SX;
+    const long long pc = pidx(g, 0, 0, x0 - HS + lx, y0 - HS + ly, 0);
+    sl[ly][lx] = f.lam[pc];
+    sm[ly][lx] = f.mu[pc];
+  }
+  __syncthreads();
+  // stresses on the tile +- HS (nodes of the full grid only)
+  for (int i = tid; i < SX * SY; i += TX * TY) {
+    const int lx = i % SX, ly = i / SX;
+    const int qx = x0 - HS + lx, qy = y0 - HS + ly;
+    T sxx = T(0), syy = T(0), sxy = T(0);
+    if (qx >= 0 && qx < nx && qy >= 0 && qy < ny) {
+      const int ux = lx + (HU - HS), uy = ly + (HU - HS);
+      const T u_x = sbp_d1<T>(&su[0][uy][ux], 1, qx, nx);
+      const T u_y = sbp_d1<T>(&su[0][uy][ux], UX, qy, ny);
+      const T v_x = sbp_d1<T>(&su[1][uy][ux], 1, qx, nx);
+      const T v_y = sbp_d1<T>(&su[1][uy][ux], UX, qy, ny);
+      const T l = sl[ly][lx], m = sm[ly][lx];
+      const T div = u_x + v_y;
+      sxx = l * div + T(2) * m * u_x;
+      syy = l * div + T(2) * m * v_y;
+      sxy = m * (u_y + v_x);
+    }
+    ss[0][ly][lx] = sxx;
+    ss[1][ly][lx] = syy;
+    ss[2][ly][lx] = sxy;
+  }
+  __syncthreads();
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  if (!is_unknown(g, x, y, 0)) return;
+  const int lx = threadIdx.x + HS, ly = threadIdx.y + HS;
+  const T inv_h0 = T(48.0 / 17.0);
+  // K u_x = -D_x sxx - D_y sxy (+ boundary terms on free sides)
+  T ku = -sbp_d1<T>(&ss[0][ly][lx], 1, x, nx) - sbp_d1<T>(&ss[2][ly][lx], SX, y, ny);
+  T kv = -sbp_d1<T>(&ss[2][ly][lx], 1, x, nx) - sbp_d1<T>(&ss[1][ly][lx], SX, y, ny);
+  if (x == 0) {
+    ku -= inv_h0 * ss[0][ly][lx];
+    kv -= inv_h0 * ss[2][ly][lx];
+  } else if (x == nx - 1) {
+    ku += inv_h0 * ss[0][ly][lx];
+    kv += inv_h0 * ss[2][ly][lx];
+  }
+  if (y == 0) {
+    ku -= inv_h0 * ss[2][ly][lx];
+    kv -= inv_h0 * ss[1][ly][lx];
+  } else if (y == ny - 1) {
+    ku += inv_h0 * ss[2][ly][lx];
+    kv += inv_h0 * ss[1][ly][lx];
+  }
+  const T irh = f.irh2[pidx(g, 0, 0, x, y, 0)];
+  const long long p0 = pidx(g, rhs, 0, x, y, 0);
+  leapfrog_update<T, MODE, FORCED>(f, p0, su[0][threadIdx.y + HU][threadIdx.x + HU], ku * irh, s);
+  leapfrog_update<T, MODE, FORCED>(f, p0 + g.field, su[1][threadIdx.y + HU][threadIdx.x + HU], kv * irh, s);
+}
+
+// ---------------------------------------------------------------------------
+// Order 4 (SBP), 2D, streaming: one launch per time level.  A CTA of 32 x 8
+// threads owns a 32-node column strip of SROWS rows and walks down it 8 rows
+// at a time.  Shared-memory ring buffers of 16 rows hold u (x-halo 6) and the
+// stresses (x-halo 3); per 8 output rows it loads 8 new u rows, forms 8 new
+// stress rows (3 rows ahead) and updates the 8 rows.  Halo overhead is only in
+// x (44/32 u loads, 38/32 stresses) plus 9 rows per strip.
+// ---------------------------------------------------------------------------
+constexpr int ST_TX = 32, ST_TY = 8, ST_RING = 16, ST_HU = 6, ST_HS = 3;
+constexpr int ST_UX = ST_TX + 2 * ST_HU, ST_SX = ST_TX + 2 * ST_HS;
+constexpr int ST_SROWS = 64;
+
+// SBP first derivative along y on a ring of rows: row r lives in slot r & 15.
+template <typename T>
+__device__ __forceinline__ T sbp_d1_ring(const T* base, int row_stride, int q, int N) {
+  auto at = [&](int r) -> T { return base[(r & (ST_RING - 1)) * row_stride]; };
+  if (q < 4) {
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) acc += sbp_coef<T>(q, j) * at(j);
+    return acc;
+  }
+  if (q > N - 5) {
+    const int r = N - 1 - q;
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) acc -= sbp_coef<T>(r, j) * at(N - 1 - j);
+    return acc;
+  }
+  return (at(q - 2) - T(8) * at(q - 1) + T(8) * at(q + 1) - at(q + 2)) * T(1.0 / 12.0);
+}
+
+template <typename T, int MODE, bool FORCED>
+__global__ void __launch_bounds__(256) step2d_o4_stream(Geom g, WaveFields<T> f, StepScalars s) {
+  if (g.dim != 2) return;
+  __shared__ T ur[2][ST_RING][ST_UX];
+  __shared__ T sr[3][ST_RING][ST_SX];
+  const int rhs = blockIdx.z;
+  const int x0 = blockIdx.x * ST_TX;
+  const int ys = blockIdx.y * ST_SROWS;
+  const int nx = g.n[0], ny = g.n[1];
+  const int yend = min(ys + ST_SROWS, ny);  // output rows [ys, yend)
+  const int tid = threadIdx.y * ST_TX + threadIdx.x;
+  const long long comp_off = g.field;
+  const T* ubase = f.u_cur + (long long)(rhs * g.dim) * g.field;  // start of (rhs, comp 0)
+
+  // u rows [r0, r1) into the ring (zero outside the grid)
+  auto load_u = [&](int r0, int r1) {
+    const int cnt = (r1 - r0) * ST_UX;
+    for (int i = tid; i < cnt; i += ST_TX * ST_TY) {
+      const int lx = i % ST_UX, r = r0 + i / ST_UX;
+      T a = T(0), b = T(0);
+      if (r >= 0 && r < ny) {
+        const long long off = (long long)(r + PAD) * g.np[0] + (x0 - ST_HU + lx + PAD);
+        a = ubase[off];
+        b = ubase[off + comp_off];
+      }
+      ur[0][r & (ST_RING - 1)][lx] = a;
+      ur[1][r & (ST_RING - 1)][lx] = b;
+    }
+  };
+  // stress rows [q0, q1) from the u ring
+  auto stress = [&](int q0, int q1) {
+    const int cnt = (q1 - q0) * ST_SX;
+    for (int i = tid; i < cnt; i += ST_TX * ST_TY) {
+      const int lx = i % ST_SX, q = q0 + i / ST_SX;
+      const int qx = x0 - ST_HS + lx;
+      T sxx = T(0), syy = T(0), sxy = T(0);
+      if (q >= 0 && q < ny && qx >= 0 && qx < nx) {
+        const int ux = lx + (ST_HU - ST_HS);
+        const int slot = q & (ST_RING - 1);
+        const T u_x = sbp_d1<T>(&ur[0][slot][ux], 1, qx, nx);
+        const T v_x = sbp_d1<T>(&ur[1][slot][ux], 1, qx, nx);
+        const T u_y = sbp_d1_ring<T>(&ur[0][0][ux], ST_UX, q, ny);
+        const T v_y = sbp_d1_ring<T>(&ur[1][0][ux], ST_UX, q, ny);
+        const long long pc = pidx(g, 0, 0, qx, q, 0);
+        const T l = f.lam[pc], m = f.mu[pc];
+        const T div = u_x + v_y;
+        sxx = l * div + T(2) * m * u_x;
+        syy = l * div + T(2) * m * v_y;
+        sxy = m * (u_y + v_x);
+      }
+      const int slot = q & (ST_RING - 1);
+      sr[0][slot][lx] = sxx;
+      sr[1][slot][lx] = syy;
+      sr[2][slot][lx] = sxy;
+    }
+  };
+
+  // prologue: u rows [ys-6, ys+6), stresses [ys-3, ys+3)
+  load_u(ys - ST_HU, ys + ST_HU);
+  __syncthreads();
+  stress(ys - ST_HS, ys + ST_HS);
+  const T inv_h0 = T(48.0 / 17.0);
+  for (int j0 = ys; j0 < yend; j0 += ST_TY) {
+    load_u(j0 + ST_HU, j0 + ST_HU + ST_TY);        // u rows j0+6 .. j0+13
+    __syncthreads();
+    stress(j0 + ST_HS, j0 + ST_HS + ST_TY);        // stresses j0+3 .. j0+10
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = j0 + threadIdx.y;
+    if (y < yend && is_unknown(g, x, y, 0)) {
+      const int lx = threadIdx.x + ST_HS;
+      const int slot = y & (ST_RING - 1);
+      T ku = -sbp_d1<T>(&sr[0][slot][lx], 1, x, nx) - sbp_d1_ring<T>(&sr[2][0][lx], ST_SX, y, ny);
+      T kv = -sbp_d1<T>(&sr[2][slot][lx], 1, x, nx) - sbp_d1_ring<T>(&sr[1][0][lx], ST_SX, y, ny);
+      if (x == 0) {
+        ku -= inv_h0 * sr[0][slot][lx];
+        kv -= inv_h0 * sr[2][slot][lx];
+      } else if (x == nx - 1) {
+        ku += inv_h0 * sr[0][slot][lx];
+        kv += inv_h0 * sr[2][slot][lx];
+      }
+      if (y == 0) {
+        ku -= inv_h0 * sr[2][slot][lx];
+        kv -= inv_h0 * sr[1][slot][lx];
+      } else if (y == ny - 1) {
+        ku += inv_h0 * sr[2][slot][lx];
+        kv += inv_h0 * sr[1][slot][lx];
+      }
+      const T irh = f.irh2[pidx(g, 0, 0, x, y, 0)];
+      const long long p0 = pidx(g, rhs, 0, x, y, 0);
+      leapfrog_update<T, MODE, FORCED>(f, p0, f.u_cur[p0], ku * irh, s);
+      leapfrog_update<T, MODE, FORCED>(f, p0 + g.field, f.u_cur[p0 + g.field], kv * irh, s);
+    }
+    // the next iteration overwrites stress slots of rows j0-5 .. j0+2, read above
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// 2D order-4 kernel variant: 0 = stress + divergence launches (default,
+// measured faster on GB300), 1 = single fused launch.  EWH_STEP2D_O4=fused
+// selects the latter; it is read whenever launches are enqueued (a context
+// captures its step graph once, on first use).
+static int step2d_o4_variant() {
+  const char* e = getenv("EWH_STEP2D_O4");
+  if (e && e[0] == 'f') return 1;
+  if (e && e[0] == 's' && e[1] == 't') return 2;
+  return 0;
+}
+
 template <typename T, int MODE, bool FORCED>
 static cudaError_t launch_mode(const Geom& g, int order, const WaveFields<T>& f, const StepScalars& s,
                                cudaStream_t st, long long* nl) {
@@ -375,6 +607,19 @@ static cudaError_t launch_mode(const Geom& g, int order, const WaveFields<T>& f,
       dim3 blk(32, 4, 2), grd((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, ((g.n[2] + 1) / 2) * g.nrhs);
       step3d_o2<T, MODE, FORCED><<<grd, blk, 0, st>>>(g, f, s);
     }
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+  }
+  if (g.dim == 2 && step2d_o4_variant() == 2) {
+    dim3 blk(ST_TX, ST_TY), grd((g.n[0] + ST_TX - 1) / ST_TX, (g.n[1] + ST_SROWS - 1) / ST_SROWS, g.nrhs);
+    step2d_o4_stream<T, MODE, FORCED><<<grd, blk, 0, st>>>(g, f, s);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+  }
+  if (g.dim == 2 && step2d_o4_variant() == 1) {
+    constexpr int TY = o4_tile_y<T>();
+    dim3 blk(32, TY), grd((g.n[0] + 31) / 32, (g.n[1] + TY - 1) / TY, g.nrhs);
+    step2d_o4_fused<T, MODE, FORCED><<<grd, blk, 0, st>>>(g, f, s);
     if (nl) *nl += 1;
     return cudaGetLastError();
   }

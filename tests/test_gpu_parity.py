@@ -258,3 +258,22 @@ def test_layered_1024_fp64_sampled_parity():
     nn = p.n_nodes()
     gv = np.array([got[c * nn + idx[node[1], node[0]]] for c in range(2)])
     assert np.abs(gv - want).max() <= TOL64 * np.abs(got).max(), (gv, want)
+
+
+@pytest.mark.parametrize("variant", ["split", "fused", "stream"])
+@pytest.mark.parametrize("shape", [[45, 19], [70, 131]])
+def test_order4_2d_kernel_variants_match_oracle(variant, shape, monkeypatch):
+    """Every 2D order-4 step kernel (stress + divergence launches, the fused
+    tile launch, the streaming column launch) reproduces the oracle S apply,
+    FP64 and FP32; 131 rows span several 64-row strips with a ragged last one."""
+    monkeypatch.setenv("EWH_STEP2D_O4", variant)
+    p = inputs.small_problem(2, shape, 4, [1, 0, 0, 1], seed=17, nrhs=2)
+    s = O.build_system(p)
+    v = inputs.random_vectors(p, 1, 18)[0]
+    want = oracle_all_rhs(s, lambda ss, x, r: O.apply_S(ss, x, r), v)
+    with _wh(p) as wh:
+        assert rel_err(to_np(wh.apply_S(v)), want) < TOL64
+        kinds = wh.kernel_launches()
+    with _wh(p, "fp32") as wh:
+        assert rel_err(to_np(wh.apply_S(v)), want) < tol32(s.nt)
+    assert kinds > 0
