@@ -185,6 +185,36 @@ ewh_status ewh_get_stats(ewh_ctx* ctx, ewh_stats* out);
 /* Zero the accumulated statistics (the launch counter included). */
 ewh_status ewh_reset_stats(ewh_ctx* ctx);
 
+/* Allocation-free weighted inner products (no counterpart in the paper; a
+ * convenience for callers that must not allocate device memory).
+ *
+ * Some callers cannot call cudaMalloc: code running while a CUDA graph is
+ * being captured (allocation would break or be baked into the capture),
+ * embedded or real-time hosts that reserve all device memory up front,
+ * and frameworks whose own memory pool owns the device.  This entry point
+ * needs no context (ewh_create allocates) and allocates nothing: its
+ * per-block partial sums live in one fixed array inside libewh.so that every
+ * GPU loading the library keeps until the process exits (64 KiB per device).
+ *
+ *   out[b] = sum_{c < ncomp} sum_{i < nodes} w[i] * x[b][c][i] * y[b][c][i]
+ *
+ * for b < nbatch, with x, y laid out [nbatch][ncomp][nodes] like the solver's
+ * vectors and w one weight per node (e.g. the mass diagonal).  The sums use the
+ * same fixed-order two-pass reduction as ewh_mdot.
+ *   x, y, w, out  device pointers; out receives nbatch doubles.
+ *   cuda_stream   the stream the two kernels run on (NULL = legacy default).
+ * Limits: nbatch <= 128 (EWH_EINVAL beyond, with a message in
+ * ewh_last_error(NULL)); nodes, ncomp >= 1.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (different streams without ordering) race and may return
+ * wrong sums, so order them.  Nothing needs clearing between calls: each call
+ * writes every partial sum it reads.  Returns EWH_OK, EWH_EINVAL or
+ * EWH_ECUDA; results are ready when the stream reaches them. */
+ewh_status ewh_mdot_noalloc(const double* x, const double* y, const double* w, long long nodes, int ncomp,
+                            int nbatch, double* out, void* cuda_stream);
+
 /* Release every resource of the context (NULL is ignored). */
 void ewh_destroy(ewh_ctx* ctx);
 

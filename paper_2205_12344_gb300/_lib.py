@@ -57,6 +57,7 @@ SIGNATURES = {
     "ewh_kernel_launches": (ctypes.c_longlong, [_P]),
     "ewh_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ewh_stats)]),
     "ewh_reset_stats": (ctypes.c_int, [_P]),
+    "ewh_mdot_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _P, _P]),
     "ewh_destroy": (None, [_P]),
     "ewh_last_error": (ctypes.c_char_p, [_P]),
     "ewh_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -173,6 +174,13 @@ def ewh_get_stats(ctx):
 
 def ewh_reset_stats(ctx):
     return _check(load().ewh_reset_stats(ctx), ctx)
+
+
+def ewh_mdot_noalloc(x, y, w, nodes, ncomp, nbatch, out, stream=None):
+    """Allocation-free weighted inner products into the device array ``out``."""
+    st = ctypes.c_void_p(stream) if stream else None
+    return _check(load().ewh_mdot_noalloc(_ptr(x), _ptr(y), _ptr(w), int(nodes), int(ncomp), int(nbatch),
+                                          _ptr(out), st))
 
 
 def ewh_destroy(ctx):

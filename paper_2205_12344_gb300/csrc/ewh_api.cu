@@ -90,6 +90,12 @@ namespace {
     }                                                                                  \
   } while (0)
 
+}  // namespace
+
+void ewh::set_global_error(const std::string& msg) { g_create_error = msg; }
+
+namespace {
+
 ewh_status fail(ewh_ctx* ctx, ewh_status s, const std::string& msg) {
   if (ctx) ctx->err = msg;
   else g_create_error = msg;

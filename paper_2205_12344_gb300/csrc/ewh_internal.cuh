@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace ewh {
 
 // Padding (ghost layers, always zero) around the full node grid of every
@@ -113,5 +115,8 @@ cudaError_t launch_cg_replace(int nrhs, const double* dot, double* rr, double* b
 cudaError_t launch_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t st);
 cudaError_t launch_fill_mass(const Geom& g, int order, const double* rho_full, double h, double* mw,
                              cudaStream_t st);
+
+// Message for ewh_last_error(NULL) of calls that have no context.
+void set_global_error(const std::string& msg);
 
 }  // namespace ewh

@@ -5,6 +5,8 @@
 // adds the per-block partial sums in a fixed order.
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "ewh_internal.cuh"
 
 namespace ewh {
@@ -296,6 +298,108 @@ cudaError_t launch_fill_mass(const Geom& g, int order, const double* rho_full, d
   fill_mass_kernel<<<grid_for(g.nodes), 256, 0, st>>>(g, order, rho_full, hd, mw);
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Weighted inner products without any allocation (ewh_mdot_noalloc).
+//
+// Same deterministic two-pass reduction as the context's M inner product,
+// but the per-block partial sums live in a file-scope device array instead of
+// context-owned memory, so the call allocates nothing.  Capacity:
+// NOALLOC_BLOCKS blocks per batch member, at most NOALLOC_MAX_BATCH members.
+// ---------------------------------------------------------------------------
+constexpr int NOALLOC_BLOCKS = 64;
+constexpr int NOALLOC_MAX_BATCH = 128;
+static __device__ __align__(256) double g_noalloc_partials[NOALLOC_BLOCKS * NOALLOC_MAX_BATCH];
+
+__global__ void noalloc_partial_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                                       const double* __restrict__ w, long long nodes, int ncomp,
+                                       double* __restrict__ part) {
+  const int b = blockIdx.y;
+  const long long n = (long long)ncomp * nodes;
+  const double* xb = x + (long long)b * n;
+  const double* yb = y + (long long)b * n;
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)RED_THREADS + threadIdx.x; i < n;
+       i += (long long)gridDim.x * RED_THREADS)
+    s += w[i % nodes] * xb[i] * yb[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[(long long)b * NOALLOC_BLOCKS + blockIdx.x] = s;
+}
+
+__global__ void noalloc_final_kernel(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+  const int b = blockIdx.x;
+  const double s = sum_partials(part + (long long)b * NOALLOC_BLOCKS, nblk);
+  if (threadIdx.x == 0) out[b] = s;
+}
+
+}  // namespace ewh
+
+#include <mutex>
+
+#include "../../include/ewh.h"
+
+namespace {
+// Device address of g_noalloc_partials, fetched once per device with that
+// device current (in host code the symbol itself is only a host stand-in).
+constexpr int MAX_DEVICES = 64;
+double* g_noalloc_ptr[MAX_DEVICES] = {nullptr};
+std::mutex g_noalloc_mutex;
+}  // namespace
+
+extern "C" ewh_status ewh_mdot_noalloc(const double* x, const double* y, const double* w, long long nodes,
+                                       int ncomp, int nbatch, double* out, void* cuda_stream) {
+  using namespace ewh;
+  if (!x || !y || !w || !out) {
+    set_global_error("ewh_mdot_noalloc: null pointer argument");
+    return EWH_EINVAL;
+  }
+  if (nodes < 1 || ncomp < 1 || nbatch < 1) {
+    set_global_error("ewh_mdot_noalloc: nodes, ncomp and nbatch must be >= 1");
+    return EWH_EINVAL;
+  }
+  if (nbatch > NOALLOC_MAX_BATCH) {
+    set_global_error("ewh_mdot_noalloc: nbatch exceeds the fixed scratch capacity of 128 batch members");
+    return EWH_EINVAL;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+    cudaGetLastError();
+    set_global_error("ewh_mdot_noalloc: no usable current CUDA device");
+    return EWH_ECUDA;
+  }
+  double* part = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        set_global_error(std::string("ewh_mdot_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+        return EWH_ECUDA;
+      }
+      g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    part = g_noalloc_ptr[dev];
+  }
+  const long long n = (long long)ncomp * nodes;
+  long long nb = (n + 4 * RED_THREADS - 1) / (4 * RED_THREADS);
+  if (nb > NOALLOC_BLOCKS) nb = NOALLOC_BLOCKS;
+  if (nb < 1) nb = 1;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // every partial slot read by the final pass is written by the first one, so
+  // nothing left over from an earlier call needs clearing
+  noalloc_partial_kernel<<<dim3((unsigned)nb, (unsigned)nbatch), RED_THREADS, 0, st>>>(x, y, w, nodes, ncomp, part);
+  noalloc_final_kernel<<<nbatch, RED_THREADS, 0, st>>>(part, (int)nb, out);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_global_error(std::string("ewh_mdot_noalloc: launch failed: ") + cudaGetErrorString(e));
+    return EWH_ECUDA;
+  }
+  return EWH_OK;
+}
+
+namespace ewh {
 
 template cudaError_t launch_pack<float>(const Geom&, const double*, float*, cudaStream_t);
 template cudaError_t launch_pack<double>(const Geom&, const double*, double*, cudaStream_t);
