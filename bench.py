@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--iters", type=int, default=100, help="CG iterations per step")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the plain FP64 GPU solve used for the time-to-tol comparison")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched 192-system measurement")
+    ap.add_argument("--batch-iters", type=int, default=24, help="batched CG iterations timed")
     return ap.parse_args()
 
 
@@ -68,10 +70,10 @@ def dist_info():
 
 
 def workload(nu, rank, world):
-    from paper_2205_12344_gb300 import inputs
-    # each rank's shot sits at its own horizontal position (independent problems)
+    from paper_2205_12344_gb300 import inputs, parallel
+    # each rank solves its own shot (independent problems, weak scaling)
     L = (nu + 1) * 0.01
-    shot = L * (rank + 1) / (world + 1)
+    shot = parallel.shot_positions(L, world)[parallel.shard(world, rank, world)[0]]
     return inputs.cfg_layered_2d(nu=nu, order=4, shot_x=[shot])
 
 
@@ -210,6 +212,51 @@ def time_to_tol_table(flush, stream):
     return out
 
 
+def batch_members(nu_list=(256, 384, 512), scales=(0.5, 0.75, 1.0), shots=64):
+    """64 shots x 3 frequencies on layered media of 256^2, 384^2 and 512^2
+    unknowns (h = 10 m, same layered profile): shot i sits on size i mod 3, at
+    evenly spaced surface positions; one member per (size, frequency) carrying
+    its size's shots as right-hand sides (192 systems in 9 members)."""
+    from paper_2205_12344_gb300 import inputs, parallel
+    members = []
+    for si, nu in enumerate(nu_list):
+        nshots = len(range(si, shots, len(nu_list)))
+        xs = parallel.shot_positions((nu + 1) * 0.01, nshots)
+        for sc in scales:
+            members.append(inputs.cfg_layered_2d(nu=nu, order=4, nrhs=nshots, shot_x=xs, omega_scale=sc))
+    return members
+
+
+def batch_measurement(iters, stream):
+    """Throughput of the batched mixed-precision solve: Pi 0 setup of every
+    member plus ``iters`` batched CG iterations (every member advances one
+    FP32 S apply per iteration), timed with CUDA events."""
+    import torch
+    from paper_2205_12344_gb300.api import WaveHoltzBatch
+    members = batch_members()
+    systems = sum(p.nrhs for p in members)
+    with WaveHoltzBatch(members, "fp32") as wb:
+        wb.solve(tol=1e-6, maxit=2, raise_on_error=False)          # warm: graphs, autotuner
+        torch.cuda.synchronize()
+        l0 = wb.kernel_launches()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xs, infos = wb.solve(tol=1e-6, maxit=iters, raise_on_error=False)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = wb.kernel_launches() - l0
+        levels = 0
+        for p, inf, info in zip(members, infos, wb.infos):
+            levels += (inf.s_applies + inf.s_applies_fp64) * info.nt * p.nrhs * info.nodes
+    return {"workload": "64 shots x 3 frequencies (0.5, 0.75, 1.0 x w10) on layered 256^2/384^2/512^2, "
+                        "order 4, FP32 stencil + FP64 CG, 9 members / 192 systems",
+            "systems": systems, "iters": iters, "seconds": ms / 1e3,
+            "value": levels / (ms * 1e-3) / 1e9, "unit": UNIT, "gpu_launches": launches,
+            "max_rel_res": max(i.rel_res for i in infos)}
+
+
 def run_reference(args, ws, rank):
     """--impl reference: the FP64 CPU oracle as it stands, on host cores."""
     if rank != 0:
@@ -299,13 +346,8 @@ def main():
     st = wh.stats()
     total_ms = sum(step_ms)
     updates = (st.steps[0] + st.steps[1]) * nodes
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        u = torch.tensor([float(updates)], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(u)
-        updates = float(u.item())
+    from paper_2205_12344_gb300 import parallel
+    total_ms, updates = parallel.reduce_job(total_ms, updates, device="cuda")
     value = updates / (total_ms * 1e-3) / 1e9
     # dominant kernel: the FP32 leapfrog step (stress + divergence/update launches)
     step_dev_ms = st.wave_ms[1] / max(st.steps[1], 1)
@@ -328,6 +370,9 @@ def main():
         extra["s_applies_fp64_per_step"] = infos[-1].s_applies_fp64
         if not args.no_fp64_compare:
             extra["time_to_tol"] = time_to_tol_table(flush, stream)
+        if not args.no_batch:
+            flush.fill_(1.0)
+            extra["batch"] = batch_measurement(args.batch_iters, stream)
     wh.close()
 
     # end to end through the C ABI with host buffers: create (H2D of medium and

@@ -94,6 +94,9 @@ typedef struct {
   long long n_unknowns;/* dim * nodes (one right-hand side) */
   int nrhs;
   int nu[3];           /* unknown nodes per axis */
+  int kernel_variant[2]; /* step-kernel variant picked by the autotuner for the
+                            FP64 / FP32 wave solves (-1 = not picked yet; it is
+                            picked on the first solve of that precision) */
 } ewh_problem_info;
 
 typedef struct {
@@ -185,6 +188,52 @@ ewh_status ewh_get_stats(ewh_ctx* ctx, ewh_stats* out);
 /* Zero the accumulated statistics (the launch counter included). */
 ewh_status ewh_reset_stats(ewh_ctx* ctx);
 
+/* ---- Batches: many independent problems advanced together ----------------
+ *
+ * Shots at different sources, frequencies and grid sizes are independent
+ * El-WaveHoltz problems.  A batch advances all of them together: one CG
+ * iteration of every unconverged member is one CUDA graph in which each member
+ * is a parallel branch (its pack, its nt*periods leapfrog launches, its FP64
+ * Krylov updates), so small members fill the GPU together and the whole
+ * iteration costs one launch.  Converged members drop out of the graph.
+ * Members must share dim, order and precision; sizes, media, frequencies and
+ * right-hand-side counts may differ. */
+typedef struct ewh_batch ewh_batch;
+
+typedef struct {
+  ewh_grid_desc desc;     /* as for ewh_create */
+  const double* rho;      /* host or device, full grid */
+  const double* lambda;
+  const double* mu;
+  double omega;
+  const double* forcing;  /* [nrhs][dim][full grid], required for solves */
+  int nrhs;
+} ewh_problem;
+
+/* Create a batch of nprob >= 1 problems (each is validated as by ewh_create). */
+ewh_status ewh_batch_create(const ewh_problem* probs, int nprob, void* cuda_stream, ewh_batch** out);
+
+/* v_out[k] = S v_in[k] for every member k (device FP64 vectors, member layout). */
+ewh_status ewh_batch_apply_S(ewh_batch* b, const double* const* v_in, double* const* v_out);
+
+/* Solve every member as ewh_solve does (same tolerance and stopping rule);
+ * v_out[k] receives member k's solution (host or device FP64), infos[k] its
+ * statistics (optional).  Returns EWH_OK when every member converged, else the
+ * first failing member's status (the others are still solved). */
+ewh_status ewh_batch_solve(ewh_batch* b, double tol, int maxit, double* const* v_out, ewh_solve_info* infos);
+
+/* The context of member k (owned by the batch; use for ewh_get_info). */
+ewh_status ewh_batch_member(ewh_batch* b, int k, ewh_ctx** ctx);
+
+/* Kernel launches issued by the batch (all members, graphs included). */
+long long ewh_batch_kernel_launches(const ewh_batch* b);
+
+/* Message of the batch's last failing call. */
+const char* ewh_batch_last_error(const ewh_batch* b);
+
+/* Release the batch and its member contexts (NULL is ignored). */
+void ewh_batch_destroy(ewh_batch* b);
+
 /* Allocation-free weighted inner products (no counterpart in the paper; a
  * convenience for callers that must not allocate device memory).
  *
@@ -214,6 +263,67 @@ ewh_status ewh_reset_stats(ewh_ctx* ctx);
  * EWH_ECUDA; results are ready when the stream reaches them. */
 ewh_status ewh_mdot_noalloc(const double* x, const double* y, const double* w, long long nodes, int ncomp,
                             int nbatch, double* out, void* cuda_stream);
+
+/* ---- Layers of the learned warm start --------------------------------------
+ *
+ * The paper has no learned component: these entry points serve the warm-start
+ * form of the solver (an initial guess x0 for ewh_solve from a small
+ * convolutional encoder-decoder over medium, forcing and frequency).
+ * Conventions: activations NHWC, weights [Co][3][3][Ci]; tensors typed void*
+ * hold bfloat16, float* hold FP32; all pointers are device pointers; the work
+ * is enqueued on `stream` (NULL = legacy default stream) and nothing is
+ * allocated.  Errors: EWH_EINVAL (bad sizes, message in ewh_last_error(NULL)),
+ * EWH_ECUDA. */
+
+/* y = conv3x3(x, w) + bias (zero padding, stride 1), BF16 tensor-core MMA with
+ * FP32 accumulation.  y_pre (FP32, may be NULL) receives the pre-activation,
+ * y_act (BF16, may be NULL) the activation (act = 1: leaky ReLU 0.1, 0: none).
+ * Ci a multiple of 16, Co a multiple of 8; bias may be NULL. */
+ewh_status ewh_conv3x3_fwd(const void* x, const void* w, const float* bias, float* y_pre, void* y_act, int act,
+                           int N, int H, int W, int Ci, int Co, void* stream);
+
+/* dx = gradient with respect to x of <conv3x3(x, w), dy> (FP32 out, BF16 dy).
+ * w_scratch: caller buffer of 9*Ci*Co bf16 for the flipped weights.  Ci, Co
+ * multiples of 16. */
+ewh_status ewh_conv3x3_dgrad(const void* dy, const void* w, void* w_scratch, float* dx, int N, int H, int W, int Ci,
+                             int Co, void* stream);
+
+/* dw (FP32, overwritten) = gradient with respect to w of <conv3x3(x, w), dy>.
+ * x, dy BF16.  Ci, Co multiples of 16. */
+ewh_status ewh_conv3x3_wgrad(const void* x, const void* dy, float* dw, int N, int H, int W, int Ci, int Co,
+                             void* stream);
+
+/* db[c] = sum over the P pixels of dy[p][c] (FP32). */
+ewh_status ewh_bias_grad(const float* dy, float* db, long long P, int C, void* stream);
+
+/* Leaky-ReLU gradient from the FP32 pre-activation: dx = dy (pre > 0) or
+ * 0.1 dy; written in FP32 (dx) and/or BF16 (dx_bf16). */
+ewh_status ewh_leaky_relu_bwd(const float* pre, const float* dy, float* dx, void* dx_bf16, long long n,
+                              void* stream);
+
+/* 2x2 average pooling of BF16 NHWC x (H, W even) and its FP32 gradient. */
+ewh_status ewh_avgpool2(const void* x, void* y, int N, int H, int W, int C, void* stream);
+ewh_status ewh_avgpool2_bwd(const float* dy, float* dx, int N, int H, int W, int C, void* stream);
+
+/* Nearest 2x upsampling of x [N,H,W,C] into channels [c_off, c_off+C) of
+ * y [N,2H,2W,Cy] (BF16), and its FP32 gradient. */
+ewh_status ewh_upsample2(const void* x, void* y, int N, int H, int W, int C, int Cy, int c_off, void* stream);
+ewh_status ewh_upsample2_bwd(const float* dy, float* dx, int N, int H, int W, int C, int Cy, int c_off,
+                             void* stream);
+
+/* Channel concatenation: copy BF16 x [P][C] into channels [c_off, c_off+C) of
+ * y [P][Cy]; and the FP32 gradient slice dx (=, or += if accumulate) dy[.][c_off..]. */
+ewh_status ewh_copy_channels(const void* x, void* y, long long P, int C, int Cy, int c_off, void* stream);
+ewh_status ewh_slice_channels(const float* dy, float* dx, long long P, int C, int Cy, int c_off, int accumulate,
+                              void* stream);
+
+/* FP32 -> BF16 conversion of n values. */
+ewh_status ewh_f32_to_bf16(const float* a, void* b, long long n, void* stream);
+
+/* One Adam step (Kingma and Ba 2015, bias-corrected, step >= 1) on FP32
+ * parameters; param_bf16 (may be NULL) receives the updated BF16 copy. */
+ewh_status ewh_adam_step(float* param, const float* grad, float* m, float* v, void* param_bf16, long long n,
+                         float lr, float beta1, float beta2, float eps, int step, void* stream);
 
 /* Release every resource of the context (NULL is ignored). */
 void ewh_destroy(ewh_ctx* ctx);

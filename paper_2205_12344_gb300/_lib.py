@@ -26,7 +26,7 @@ class ewh_problem_info(ctypes.Structure):
     _fields_ = [("nt", ctypes.c_int), ("periods", ctypes.c_int), ("dt", ctypes.c_double),
                 ("omega", ctypes.c_double), ("omega_tilde", ctypes.c_double), ("kt", ctypes.c_double),
                 ("nodes", ctypes.c_longlong), ("n_unknowns", ctypes.c_longlong), ("nrhs", ctypes.c_int),
-                ("nu", ctypes.c_int * 3)]
+                ("nu", ctypes.c_int * 3), ("kernel_variant", ctypes.c_int * 2)]
 
 
 class ewh_solve_info(ctypes.Structure):
@@ -37,6 +37,12 @@ class ewh_solve_info(ctypes.Structure):
 class ewh_stats(ctypes.Structure):
     _fields_ = [("wave_ms", ctypes.c_double * 2), ("steps", ctypes.c_longlong * 2),
                 ("waves", ctypes.c_longlong * 2), ("launches", ctypes.c_longlong)]
+
+
+class ewh_problem(ctypes.Structure):
+    _fields_ = [("desc", ewh_grid_desc), ("rho", ctypes.c_void_p), ("lambda_", ctypes.c_void_p),
+                ("mu", ctypes.c_void_p), ("omega", ctypes.c_double), ("forcing", ctypes.c_void_p),
+                ("nrhs", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -58,6 +64,14 @@ SIGNATURES = {
     "ewh_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ewh_stats)]),
     "ewh_reset_stats": (ctypes.c_int, [_P]),
     "ewh_mdot_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _P, _P]),
+    "ewh_batch_create": (ctypes.c_int, [ctypes.POINTER(ewh_problem), ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    "ewh_batch_apply_S": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "ewh_batch_solve": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_P),
+                                       ctypes.POINTER(ewh_solve_info)]),
+    "ewh_batch_member": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "ewh_batch_kernel_launches": (ctypes.c_longlong, [_P]),
+    "ewh_batch_last_error": (ctypes.c_char_p, [_P]),
+    "ewh_batch_destroy": (None, [_P]),
     "ewh_destroy": (None, [_P]),
     "ewh_last_error": (ctypes.c_char_p, [_P]),
     "ewh_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -181,6 +195,63 @@ def ewh_mdot_noalloc(x, y, w, nodes, ncomp, nbatch, out, stream=None):
     st = ctypes.c_void_p(stream) if stream else None
     return _check(load().ewh_mdot_noalloc(_ptr(x), _ptr(y), _ptr(w), int(nodes), int(ncomp), int(nbatch),
                                           _ptr(out), st))
+
+
+def ewh_batch_create(problems, stream=None):
+    """problems: list of (desc, rho, lam, mu, omega, forcing, nrhs) with array arguments."""
+    arr = (ewh_problem * len(problems))()
+    for k, (desc, rho, lam, mu, omega, forcing, nrhs) in enumerate(problems):
+        arr[k].desc = desc
+        arr[k].rho = _ptr(rho)
+        arr[k].lambda_ = _ptr(lam)
+        arr[k].mu = _ptr(mu)
+        arr[k].omega = float(omega)
+        arr[k].forcing = _ptr(forcing)
+        arr[k].nrhs = int(nrhs)
+    out = ctypes.c_void_p()
+    st = ctypes.c_void_p(stream) if stream else None
+    _check(load().ewh_batch_create(arr, len(problems), st, ctypes.byref(out)))
+    return out
+
+
+def _ptr_array(tensors):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for k, t in enumerate(tensors):
+        arr[k] = _ptr(t).value
+    return arr
+
+
+def _bcheck(status, b):
+    if status != EWH_OK:
+        raise EwhError(status, load().ewh_batch_last_error(b).decode())
+    return status
+
+
+def ewh_batch_apply_S(b, v_in, v_out):
+    return _bcheck(load().ewh_batch_apply_S(b, _ptr_array(v_in), _ptr_array(v_out)), b)
+
+
+def ewh_batch_solve(b, tol, maxit, v_out, raise_on_error=True):
+    infos = (ewh_solve_info * len(v_out))()
+    s = load().ewh_batch_solve(b, float(tol), int(maxit), _ptr_array(v_out), infos)
+    if raise_on_error:
+        _bcheck(s, b)
+    return list(infos)
+
+
+def ewh_batch_member(b, k):
+    c = ctypes.c_void_p()
+    _check(load().ewh_batch_member(b, int(k), ctypes.byref(c)))
+    return c
+
+
+def ewh_batch_kernel_launches(b):
+    return int(load().ewh_batch_kernel_launches(b))
+
+
+def ewh_batch_destroy(b):
+    if b is not None:
+        load().ewh_batch_destroy(b)
 
 
 def ewh_destroy(ctx):

@@ -115,3 +115,71 @@ class WaveHoltz:
             self.close()
         except Exception:
             pass
+
+
+class WaveHoltzBatch:
+    """Independent problems (shots, frequencies, sizes) solved together: one
+    CUDA graph per CG iteration with a branch per unconverged member."""
+
+    def __init__(self, probs, precision="fp64", stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("WaveHoltzBatch needs a CUDA device (libewh.so has no CPU path)")
+        self.torch = torch
+        self.probs = list(probs)
+        self._keep = []
+        items = []
+        for p in self.probs:
+            desc = make_desc(p.dim, p.n, p.h, p.order, p.bc, PRECISIONS[precision], p.cfl, p.periods,
+                             p.corrected, 0)
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (p.rho, p.lam, p.mu, p.forcing)]
+            self._keep.append(arrs)
+            items.append((desc, arrs[0], arrs[1], arrs[2], p.omega, arrs[3], p.nrhs))
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        self.b = L.ewh_batch_create(items, s)
+        self._keep = None
+        self.infos = [L.ewh_get_info(L.ewh_batch_member(self.b, k)) for k in range(len(self.probs))]
+        self.sizes = [int(i.n_unknowns) * p.nrhs for i, p in zip(self.infos, self.probs)]
+
+    def _vecs(self, xs=None):
+        t = self.torch
+        if xs is None:
+            return [t.empty(n, dtype=t.float64, device="cuda") for n in self.sizes]
+        out = []
+        for x in xs:
+            if not isinstance(x, t.Tensor):
+                x = t.as_tensor(np.ascontiguousarray(x, dtype=np.float64))
+            out.append(x.to(device="cuda", dtype=t.float64).contiguous().reshape(-1))
+        return out
+
+    def apply_S(self, vs):
+        vin = self._vecs(vs)
+        vout = self._vecs()
+        L.ewh_batch_apply_S(self.b, vin, vout)
+        return vout
+
+    def solve(self, tol=1e-8, maxit=100000, raise_on_error=True):
+        out = self._vecs()
+        infos = L.ewh_batch_solve(self.b, tol, maxit, out, raise_on_error=raise_on_error)
+        return out, infos
+
+    def kernel_launches(self):
+        return L.ewh_batch_kernel_launches(self.b)
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            self.torch.cuda.synchronize()
+            L.ewh_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -3,6 +3,9 @@
 // M (I - S) v = M Pi 0 (Section 4.5, eq. amat_sym).
 #include <cuda_runtime.h>
 
+#include <sys/stat.h>
+#include <unistd.h>
+
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -34,6 +37,8 @@ struct Wave {
   cudaGraphExec_t graph_Pi0 = nullptr;
   long long graph_S_kernels = 0;
   long long graph_Pi0_kernels = 0;
+  int variant = -1;           // step-kernel variant (autotuner), -1 = not chosen yet
+  float variant_ms[4] = {0, 0, 0, 0};
   bool ready = false;
 };
 
@@ -63,6 +68,8 @@ struct ewh_ctx {
   int* active = nullptr;    // per rhs
   int* flags = nullptr;
   double* h_scal = nullptr; // pinned host mirror of scal
+  int* h_act = nullptr;     // pinned host mirror of active (nrhs)
+  int* h_flag = nullptr;    // pinned host mirror of flags
   int nblk = 1;
   long long launches = 0;
   std::string err = "no error";
@@ -186,10 +193,155 @@ Wave<double>& wave_of<double>(ewh_ctx* c) { return c->w64; }
 template <>
 Wave<float>& wave_of<float>(ewh_ctx* c) { return c->w32; }
 
+// ---------------------------------------------------------------------------
+// Autotuner: pick the step-kernel variant of a context by timing.
+//
+// The candidates (split or fused order-4 2D kernel; tile height of the
+// order-2 2D kernel) are timed on the context's own buffers with 2 warm-up and
+// 8 timed leapfrog levels each; the fastest wins.  Results are kept in a JSON
+// file ($EWH_TUNE_CACHE, else $HOME/.cache/ewh/tune.json) keyed by the GPU and
+// the problem's shape, so a shape is timed once per machine.  EWH_AUTOTUNE=0
+// disables timing (variant 0).
+// ---------------------------------------------------------------------------
+std::string tune_cache_path() {
+  const char* e = getenv("EWH_TUNE_CACHE");
+  if (e && e[0]) return e;
+  const char* h = getenv("HOME");
+  if (!h || !h[0]) return "";
+  return std::string(h) + "/.cache/ewh/tune.json";
+}
+
+std::vector<std::pair<std::string, int>> read_tune_cache(const std::string& path) {
+  std::vector<std::pair<std::string, int>> out;
+  FILE* f = path.empty() ? nullptr : fopen(path.c_str(), "r");
+  if (!f) return out;
+  char line[1024];
+  while (fgets(line, sizeof line, f)) {
+    char* q1 = strchr(line, '"');
+    if (!q1) continue;
+    char* q2 = strchr(q1 + 1, '"');
+    if (!q2) continue;
+    char* colon = strchr(q2, ':');
+    if (!colon) continue;
+    out.emplace_back(std::string(q1 + 1, q2), atoi(colon + 1));
+  }
+  fclose(f);
+  return out;
+}
+
+void write_tune_cache(const std::string& path, const std::vector<std::pair<std::string, int>>& kv) {
+  if (path.empty()) return;
+  const size_t slash = path.find_last_of('/');
+  if (slash != std::string::npos) {
+    std::string dir = path.substr(0, slash);
+    for (size_t i = 1; i <= dir.size(); ++i)
+      if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
+  }
+  const std::string tmp = path + ".tmp" + std::to_string((long long)getpid());
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) return;
+  fprintf(f, "{\n");
+  for (size_t i = 0; i < kv.size(); ++i)
+    fprintf(f, "  \"%s\": %d%s\n", kv[i].first.c_str(), kv[i].second, i + 1 < kv.size() ? "," : "");
+  fprintf(f, "}\n");
+  fclose(f);
+  rename(tmp.c_str(), path.c_str());
+}
+
+template <typename T>
+std::string tune_key(const ewh_ctx* ctx) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  std::string name = "gpu";
+  if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+    name = prop.name;
+    name += "-sm" + std::to_string(prop.major) + std::to_string(prop.minor) + "x" +
+            std::to_string(prop.multiProcessorCount);
+  } else {
+    cudaGetLastError();
+  }
+  for (auto& ch : name)
+    if (ch == '"' || ch == ' ') ch = '_';
+  const Geom& g = ctx->g;
+  return name + "|d" + std::to_string(g.dim) + "|o" + std::to_string(ctx->order) + "|" +
+         (sizeof(T) == 8 ? "f64" : "f32") + "|" + std::to_string(g.n[0]) + "x" + std::to_string(g.n[1]) + "x" +
+         std::to_string(g.n[2]) + "|r" + std::to_string(g.nrhs);
+}
+
+template <typename T>
+void autotune(ewh_ctx* ctx, Wave<T>& w) {
+  const int nv = step_variant_count(ctx->g.dim, ctx->order);
+  const char* off = getenv("EWH_AUTOTUNE");
+  if (nv <= 1 || (off && off[0] == '0')) {
+    w.variant = 0;
+    return;
+  }
+  const std::string path = tune_cache_path();
+  const std::string key = tune_key<T>(ctx);
+  auto cache = read_tune_cache(path);
+  for (auto& kv : cache)
+    if (kv.first == key && kv.second >= 0 && kv.second < nv) {
+      w.variant = kv.second;
+      return;
+    }
+  WaveFields<T> f{};
+  f.u_cur = w.u_a;
+  f.u_next = w.u_b;
+  f.delta = w.delta;
+  f.acc = w.acc;
+  f.lam = w.lam;
+  f.mu = w.mu;
+  f.irh2 = w.irh2;
+  f.frho = nullptr;
+  f.sigma = w.sigma;
+  StepScalars sc{ctx->kt, 1.0, 0.0, 0.0};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    w.variant = 0;
+    return;
+  }
+  int best = 0;
+  float best_ms = 1e30f;
+  for (int v = 0; v < nv; ++v) {
+    Geom g = ctx->g;
+    g.variant = v;
+    bool ok = true;
+    for (int k = 0; k < 10 && ok; ++k) {
+      if (k == 2) cudaEventRecord(e0, ctx->st);
+      ok = launch_step<T>(g, ctx->order, f, STEP_MID, sc, ctx->st, nullptr) == cudaSuccess;
+      std::swap(f.u_cur, f.u_next);
+    }
+    cudaEventRecord(e1, ctx->st);
+    float ms = 1e30f;
+    if (ok && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaGetLastError();
+    if (v < 4) w.variant_ms[v] = ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the timing levels wrote the state buffers: clear them back to zero
+  const size_t state = (size_t)ctx->g.field * ctx->g.dim * ctx->g.nrhs;
+  cudaMemsetAsync(w.u_a, 0, sizeof(T) * state, ctx->st);
+  cudaMemsetAsync(w.u_b, 0, sizeof(T) * state, ctx->st);
+  cudaMemsetAsync(w.delta, 0, sizeof(T) * state, ctx->st);
+  cudaMemsetAsync(w.acc, 0, sizeof(T) * state, ctx->st);
+  w.variant = best;
+  cache.emplace_back(key, best);
+  write_tune_cache(path, cache);
+}
+
 // Enqueue the nt*periods steps of one wave solve (u^0 already in u_a).
 template <typename T>
 cudaError_t enqueue_steps(ewh_ctx* ctx, Wave<T>& w, bool forced, long long* nl) {
   const int N = ctx->nt * ctx->periods;
+  Geom gv = ctx->g;
+  gv.variant = w.variant < 0 ? 0 : w.variant;
   WaveFields<T> f{};
   f.lam = w.lam;
   f.mu = w.mu;
@@ -208,7 +360,7 @@ cudaError_t enqueue_steps(ewh_ctx* ctx, Wave<T>& w, bool forced, long long* nl) 
     s.w0 = ctx->weights[0];
     s.wnew = ctx->weights[n + 1];
     const StepMode mode = (n == 0) ? STEP_FIRST : (n == N - 1 ? STEP_LAST : STEP_MID);
-    cudaError_t e = launch_step<T>(ctx->g, ctx->order, f, mode, s, ctx->st, nl);
+    cudaError_t e = launch_step<T>(gv, ctx->order, f, mode, s, ctx->st, nl);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -220,6 +372,7 @@ ewh_status ensure_graph(ewh_ctx* ctx, bool forced) {
   cudaGraphExec_t& ge = forced ? w.graph_Pi0 : w.graph_S;
   long long& nk = forced ? w.graph_Pi0_kernels : w.graph_S_kernels;
   if (ge) return EWH_OK;
+  if (w.variant < 0) autotune<T>(ctx, w);
   cudaGraph_t graph = nullptr;
   EWH_CU(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
   long long count = 0;
@@ -375,16 +528,22 @@ ewh_status true_residual(ewh_ctx* ctx, const double* x, double* r, double* max_r
 // replacement, or reaches tol, r is replaced by the true residual b - A64 x
 // (FP64 S apply) while the search direction is kept.  Convergence is declared
 // on the true residual only.  drop = 0 replaces only at convergence.
+//
+// The loop is split into cg_begin / cg_enqueue_iteration / cg_after_iteration
+// so that a batch of problems can put the iterations of all its members into
+// one graph and run the host-side logic per member afterwards.
+struct CgState {
+  double tol = 0.0, drop = 0.0;
+  std::vector<double> anchor, true_res;
+  bool any_active = false;
+};
+
 template <typename T>
-ewh_status run_cg(ewh_ctx* ctx, double* x, double* r, double tol, int maxit, double drop, ewh_solve_info* inf,
-                  double* rel_out) {
-  const Geom& g = ctx->g;
-  const int R = g.nrhs;
+ewh_status cg_begin(ewh_ctx* ctx, double* r, double tol, double drop, CgState& cs) {
+  const int R = ctx->g.nrhs;
   const long long n = total_unknowns(ctx);
-  Wave<T>& w = wave_of<T>(ctx);
   ewh_status st = ensure_graph<T>(ctx, false);
   if (st != EWH_OK) return st;
-  // rr = (r, r)_M ; p = 0 ; beta = 0
   st = mdot_dev(ctx, r, r, sc(ctx, S_RR));
   if (st != EWH_OK) return st;
   EWH_CU(cudaMemsetAsync(ctx->kp, 0, sizeof(double) * n, ctx->st));
@@ -392,85 +551,125 @@ ewh_status run_cg(ewh_ctx* ctx, double* x, double* r, double tol, int maxit, dou
   EWH_CU(cudaMemsetAsync(ctx->flags, 0, sizeof(int), ctx->st));
   EWH_CU(cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * S_N * R, cudaMemcpyDeviceToHost, ctx->st));
   EWH_CU(cudaStreamSynchronize(ctx->st));
-  std::vector<int> act(R, 1);
-  std::vector<double> anchor(R), true_res(R);
+  cs.tol = tol;
+  cs.drop = drop;
+  cs.anchor.assign(R, 0.0);
+  cs.true_res.assign(R, 0.0);
+  cs.any_active = false;
+  double worst = 0.0;
   for (int k = 0; k < R; ++k) {
-    true_res[k] = std::sqrt(ctx->h_scal[S_RR * R + k] / ctx->h_scal[S_BB * R + k]);
-    anchor[k] = true_res[k];
-    if (true_res[k] <= tol) act[k] = 0;
+    cs.true_res[k] = std::sqrt(ctx->h_scal[S_RR * R + k] / ctx->h_scal[S_BB * R + k]);
+    cs.anchor[k] = cs.true_res[k];
+    ctx->h_act[k] = cs.true_res[k] > tol ? 1 : 0;
+    cs.any_active = cs.any_active || ctx->h_act[k];
+    worst = std::max(worst, cs.true_res[k]);
   }
-  EWH_CU(cudaMemcpyAsync(ctx->active, act.data(), sizeof(int) * R, cudaMemcpyHostToDevice, ctx->st));
-  auto worst_true = [&]() {
-    double m = 0.0;
-    for (int k = 0; k < R; ++k) m = std::max(m, true_res[k]);
-    return m;
-  };
-  ctx->history.push_back(worst_true());
-  bool any = false;
-  for (int k = 0; k < R; ++k) any = any || act[k];
-  int it = 0;
-  while (any && inf->iters < maxit) {
-    // p = r + beta p ; u^0 = p
-    EWH_CU(launch_pupdate_pack<T>(g, r, ctx->kp, sc(ctx, S_BETA), w.u_a, ctx->st));
-    ctx->launches += 1;
+  EWH_CU(cudaMemcpyAsync(ctx->active, ctx->h_act, sizeof(int) * R, cudaMemcpyHostToDevice, ctx->st));
+  ctx->history.push_back(worst);
+  return EWH_OK;
+}
+
+// One CG iteration on ctx->st, ending with the copies of the scalars, the
+// active mask and the flags into pinned host memory.  With direct_steps the
+// leapfrog launches are enqueued one by one (inside a batch capture);
+// otherwise the context's captured S graph is launched.
+template <typename T>
+ewh_status cg_enqueue_iteration(ewh_ctx* ctx, double* x, double* r, bool direct_steps) {
+  const Geom& g = ctx->g;
+  const int R = g.nrhs;
+  Wave<T>& w = wave_of<T>(ctx);
+  // p = r + beta p ; u^0 = p
+  EWH_CU(launch_pupdate_pack<T>(g, r, ctx->kp, sc(ctx, S_BETA), w.u_a, ctx->st));
+  ctx->launches += 1;
+  if (direct_steps) {
+    long long count = 0;
+    EWH_CU(enqueue_steps<T>(ctx, w, false, &count));
+    ctx->launches += count;
+  } else {
     EWH_CU(launch_timed_graph<T>(ctx, w.graph_S));
     ctx->launches += w.graph_S_kernels;
-    // q = p - S p
-    EWH_CU(launch_unpack<T>(g, w.acc, ctx->kq, ctx->kp, ctx->st));
-    EWH_CU(launch_mdot_partial(g, ctx->mw, ctx->kp, ctx->kq, ctx->part, ctx->st));
-    EWH_CU(launch_cg_alpha(R, ctx->part, ctx->nblk, sc(ctx, S_RR), sc(ctx, S_ALPHA), ctx->active, ctx->flags,
-                           ctx->st));
-    EWH_CU(launch_cg_xr_update(g, ctx->mw, sc(ctx, S_ALPHA), ctx->kp, ctx->kq, x, r, ctx->part, ctx->st));
-    EWH_CU(launch_cg_beta(R, ctx->part, ctx->nblk, sc(ctx, S_RR), sc(ctx, S_BB), sc(ctx, S_BETA),
-                          sc(ctx, S_RES), ctx->active, ctx->st));
-    ctx->launches += 5;
-    ++it;
-    ++inf->iters;
-    if (sizeof(T) == 8) ++inf->s_applies_fp64;
-    else ++inf->s_applies;
-    int flag = 0;
-    EWH_CU(cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * S_N * R, cudaMemcpyDeviceToHost, ctx->st));
-    EWH_CU(cudaMemcpyAsync(act.data(), ctx->active, sizeof(int) * R, cudaMemcpyDeviceToHost, ctx->st));
-    EWH_CU(cudaMemcpyAsync(&flag, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-    EWH_CU(cudaStreamSynchronize(ctx->st));
-    if (flag & 1) {
-      *rel_out = worst_true();
-      return fail(ctx, EWH_EBREAKDOWN, "CG breakdown: (p, (I-S)p)_M <= 0 (indefinite system near resonance)");
-    }
-    bool replace = false;
-    double hist = 0.0;
-    for (int k = 0; k < R; ++k) {
-      const double res = ctx->h_scal[S_RES * R + k];
-      if (act[k]) {
-        hist = std::max(hist, res);
-        if (res <= tol || (drop > 0.0 && res <= drop * anchor[k])) replace = true;
-      }
-    }
-    ctx->history.push_back(hist);
-    if (replace) {
-      double dummy = 0.0;
-      st = true_residual(ctx, x, r, &dummy);
-      if (st != EWH_OK) return st;
-      ++inf->s_applies_fp64;
-      EWH_CU(launch_cg_replace(R, sc(ctx, S_DOT), sc(ctx, S_RR), sc(ctx, S_BETA), sc(ctx, S_RES), sc(ctx, S_BB),
-                               ctx->st));
-      ctx->launches += 1;
-      bool changed = false;
-      for (int k = 0; k < R; ++k) {
-        true_res[k] = std::sqrt(ctx->h_scal[S_DOT * R + k] / ctx->h_scal[S_BB * R + k]);
-        anchor[k] = true_res[k];
-        if (act[k] && true_res[k] <= tol) {
-          act[k] = 0;
-          changed = true;
-        }
-      }
-      if (changed) EWH_CU(cudaMemcpyAsync(ctx->active, act.data(), sizeof(int) * R, cudaMemcpyHostToDevice, ctx->st));
-    }
-    any = false;
-    for (int k = 0; k < R; ++k) any = any || act[k];
   }
-  *rel_out = worst_true();
-  (void)it;
+  // q = p - S p
+  EWH_CU(launch_unpack<T>(g, w.acc, ctx->kq, ctx->kp, ctx->st));
+  EWH_CU(launch_mdot_partial(g, ctx->mw, ctx->kp, ctx->kq, ctx->part, ctx->st));
+  EWH_CU(launch_cg_alpha(R, ctx->part, ctx->nblk, sc(ctx, S_RR), sc(ctx, S_ALPHA), ctx->active, ctx->flags,
+                         ctx->st));
+  EWH_CU(launch_cg_xr_update(g, ctx->mw, sc(ctx, S_ALPHA), ctx->kp, ctx->kq, x, r, ctx->part, ctx->st));
+  EWH_CU(launch_cg_beta(R, ctx->part, ctx->nblk, sc(ctx, S_RR), sc(ctx, S_BB), sc(ctx, S_BETA), sc(ctx, S_RES),
+                        ctx->active, ctx->st));
+  ctx->launches += 5;
+  EWH_CU(cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * S_N * R, cudaMemcpyDeviceToHost, ctx->st));
+  EWH_CU(cudaMemcpyAsync(ctx->h_act, ctx->active, sizeof(int) * R, cudaMemcpyDeviceToHost, ctx->st));
+  EWH_CU(cudaMemcpyAsync(ctx->h_flag, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  return EWH_OK;
+}
+
+// Host logic after an iteration whose copies have completed.
+template <typename T>
+ewh_status cg_after_iteration(ewh_ctx* ctx, double* x, double* r, CgState& cs, ewh_solve_info* inf) {
+  const int R = ctx->g.nrhs;
+  ++inf->iters;
+  if (sizeof(T) == 8) ++inf->s_applies_fp64;
+  else ++inf->s_applies;
+  if (*ctx->h_flag & 1)
+    return fail(ctx, EWH_EBREAKDOWN, "CG breakdown: (p, (I-S)p)_M <= 0 (indefinite system near resonance)");
+  bool replace = false;
+  double hist = 0.0;
+  for (int k = 0; k < R; ++k) {
+    const double res = ctx->h_scal[S_RES * R + k];
+    if (ctx->h_act[k]) {
+      hist = std::max(hist, res);
+      if (res <= cs.tol || (cs.drop > 0.0 && res <= cs.drop * cs.anchor[k])) replace = true;
+    }
+  }
+  ctx->history.push_back(hist);
+  if (replace) {
+    double dummy = 0.0;
+    ewh_status st = true_residual(ctx, x, r, &dummy);
+    if (st != EWH_OK) return st;
+    ++inf->s_applies_fp64;
+    EWH_CU(launch_cg_replace(R, sc(ctx, S_DOT), sc(ctx, S_RR), sc(ctx, S_BETA), sc(ctx, S_RES), sc(ctx, S_BB),
+                             ctx->st));
+    ctx->launches += 1;
+    bool changed = false;
+    for (int k = 0; k < R; ++k) {
+      cs.true_res[k] = std::sqrt(ctx->h_scal[S_DOT * R + k] / ctx->h_scal[S_BB * R + k]);
+      cs.anchor[k] = cs.true_res[k];
+      if (ctx->h_act[k] && cs.true_res[k] <= cs.tol) {
+        ctx->h_act[k] = 0;
+        changed = true;
+      }
+    }
+    if (changed) EWH_CU(cudaMemcpyAsync(ctx->active, ctx->h_act, sizeof(int) * R, cudaMemcpyHostToDevice, ctx->st));
+  }
+  cs.any_active = false;
+  for (int k = 0; k < R; ++k) cs.any_active = cs.any_active || ctx->h_act[k];
+  return EWH_OK;
+}
+
+double cg_worst_true(const CgState& cs) {
+  double m = 0.0;
+  for (double v : cs.true_res) m = std::max(m, v);
+  return m;
+}
+
+template <typename T>
+ewh_status run_cg(ewh_ctx* ctx, double* x, double* r, double tol, int maxit, double drop, ewh_solve_info* inf,
+                  double* rel_out) {
+  CgState cs;
+  ewh_status st = cg_begin<T>(ctx, r, tol, drop, cs);
+  if (st != EWH_OK) return st;
+  while (cs.any_active && inf->iters < maxit) {
+    st = cg_enqueue_iteration<T>(ctx, x, r, false);
+    if (st != EWH_OK) return st;
+    EWH_CU(cudaStreamSynchronize(ctx->st));
+    st = cg_after_iteration<T>(ctx, x, r, cs, inf);
+    if (st != EWH_OK) {
+      *rel_out = cg_worst_true(cs);
+      return st;
+    }
+  }
+  *rel_out = cg_worst_true(cs);
   return EWH_OK;
 }
 
@@ -552,6 +751,158 @@ ewh_status validate_desc(const ewh_grid_desc* d, int nrhs) {
 
 }  // namespace
 
+struct ewh_batch {
+  std::vector<ewh_ctx*> p;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t master = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins;
+  cudaGraphExec_t iter_graph = nullptr;
+  std::vector<int> graph_members;
+  int precision = EWH_FP64;
+  long long launches = 0;
+  std::string err = "no error";
+};
+
+namespace {
+
+ewh_status bfail(ewh_batch* b, ewh_status s, const std::string& m) {
+  b->err = m;
+  return s;
+}
+
+// Capture one graph whose branches enqueue `fn(k)` on member k's stream.
+template <typename F>
+ewh_status capture_branches(ewh_batch* b, const std::vector<int>& members, F fn, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(b->master, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return bfail(b, EWH_ECUDA, "batch capture could not start");
+  cudaError_t e = cudaEventRecord(b->fork, b->master);
+  ewh_status st = EWH_OK;
+  for (int k : members) {
+    ewh_ctx* c = b->p[k];
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->st, b->fork, 0);
+    if (e == cudaSuccess && st == EWH_OK) st = fn(k);
+    if (e == cudaSuccess) e = cudaEventRecord(b->joins[k], c->st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->master, b->joins[k], 0);
+  }
+  const cudaError_t e2 = cudaStreamEndCapture(b->master, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess || st != EWH_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (st != EWH_OK) return bfail(b, st, "batch member failed during capture: " + b->p[members.empty() ? 0 : members[0]]->err);
+    return bfail(b, EWH_ECUDA, std::string("batch capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return bfail(b, EWH_ECUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+  return EWH_OK;
+}
+
+template <typename T>
+ewh_status batch_solve_T(ewh_batch* b, double tol, int maxit, double* const* v_out, ewh_solve_info* infos) {
+  const int P = (int)b->p.size();
+  std::vector<CgState> cs(P);
+  std::vector<ewh_solve_info> inf(P);
+  std::vector<ewh_status> status(P, EWH_OK);
+  std::vector<int> fallback(P, 0);
+  const double drop = sizeof(T) == 4 ? 0.1 : 0.0;
+  const auto t0 = std::chrono::steady_clock::now();
+  // right-hand sides b = Pi 0 (FP64) and the initial residuals, per member
+  for (int k = 0; k < P; ++k) {
+    ewh_ctx* ctx = b->p[k];
+    ctx->history.clear();
+    const long long n = total_unknowns(ctx);
+    ewh_status s = run_wave<double>(ctx, nullptr, true);
+    if (s != EWH_OK) return bfail(b, s, ctx->err);
+    if (launch_unpack<double>(ctx->g, ctx->w64.acc, ctx->kb, nullptr, ctx->st) != cudaSuccess)
+      return bfail(b, EWH_ECUDA, "unpack failed");
+    ctx->launches += 1;
+    inf[k].s_applies_fp64 += 1;
+    s = mdot_dev(ctx, ctx->kb, ctx->kb, sc(ctx, S_BB));
+    if (s != EWH_OK) return bfail(b, s, ctx->err);
+    cudaMemsetAsync(ctx->kx, 0, sizeof(double) * n, ctx->st);
+    cudaMemcpyAsync(ctx->kr, ctx->kb, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->st);
+    s = cg_begin<T>(ctx, ctx->kr, tol, drop, cs[k]);
+    if (s != EWH_OK) return bfail(b, s, ctx->err);
+  }
+  std::vector<int> members;
+  for (int k = 0; k < P; ++k)
+    if (cs[k].any_active) members.push_back(k);
+  while (!members.empty()) {
+    if (members != b->graph_members || !b->iter_graph) {
+      if (b->iter_graph) cudaGraphExecDestroy(b->iter_graph);
+      b->iter_graph = nullptr;
+      ewh_status s = capture_branches(
+          b, members, [&](int k) { return cg_enqueue_iteration<T>(b->p[k], b->p[k]->kx, b->p[k]->kr, true); },
+          &b->iter_graph);
+      if (s != EWH_OK) return s;
+      b->graph_members = members;
+    }
+    if (cudaGraphLaunch(b->iter_graph, b->master) != cudaSuccess || cudaStreamSynchronize(b->master) != cudaSuccess)
+      return bfail(b, EWH_ECUDA, std::string("batch iteration failed: ") + cudaGetErrorString(cudaGetLastError()));
+    std::vector<int> next;
+    for (int k : members) {
+      ewh_ctx* ctx = b->p[k];
+      ctx->launches += 0;  // counted when captured below
+      ewh_status s = cg_after_iteration<T>(ctx, ctx->kx, ctx->kr, cs[k], &inf[k]);
+      if (s == EWH_EBREAKDOWN) {
+        fallback[k] = 1;
+        continue;
+      }
+      if (s != EWH_OK) return bfail(b, s, ctx->err);
+      if (cs[k].any_active && inf[k].iters < maxit) next.push_back(k);
+    }
+    // launches of one batched iteration: per member 1 pack + steps + 5 Krylov kernels
+    for (int k : members) {
+      const Wave<T>& w = wave_of<T>(b->p[k]);
+      b->launches += 6 + (w.graph_S_kernels ? w.graph_S_kernels : 0);
+    }
+    members.swap(next);
+  }
+  // members whose FP32 operator lost definiteness continue alone in FP64;
+  // FP64 members that broke down report it
+  for (int k = 0; k < P; ++k) {
+    ewh_ctx* ctx = b->p[k];
+    double rel = cg_worst_true(cs[k]);
+    if (fallback[k]) {
+      if (sizeof(T) == 4) {
+        ewh_status s = true_residual(ctx, ctx->kx, ctx->kr, &rel);
+        if (s != EWH_OK) return bfail(b, s, ctx->err);
+        ++inf[k].s_applies_fp64;
+        ctx->err = "no error";
+        status[k] = run_cg<double>(ctx, ctx->kx, ctx->kr, tol, maxit, 0.0, &inf[k], &rel);
+      } else {
+        status[k] = EWH_EBREAKDOWN;
+      }
+    }
+    inf[k].rel_res = rel;
+    if (status[k] == EWH_OK && !(rel <= tol)) {
+      status[k] = EWH_ENOTCONV;
+      ctx->err = "not converged: relative residual " + std::to_string(rel) + " > tol";
+    }
+    const long long n = total_unknowns(ctx);
+    if (v_out && v_out[k] &&
+        (cudaMemcpyAsync(v_out[k], ctx->kx, sizeof(double) * n, cudaMemcpyDefault, ctx->st) != cudaSuccess ||
+         cudaStreamSynchronize(ctx->st) != cudaSuccess))
+      return bfail(b, EWH_ECUDA, "copy of a batch solution failed");
+  }
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  ewh_status first = EWH_OK;
+  for (int k = 0; k < P; ++k) {
+    inf[k].seconds = secs;
+    inf[k].status = status[k];
+    if (infos) infos[k] = inf[k];
+    if (first == EWH_OK && status[k] != EWH_OK) {
+      first = status[k];
+      b->err = "member " + std::to_string(k) + ": " + b->p[k]->err;
+    }
+  }
+  return first;
+}
+
+}  // namespace
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -590,6 +941,8 @@ void ewh_destroy(ewh_ctx* ctx) {
   cudaFree(ctx->active);
   cudaFree(ctx->flags);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+  if (ctx->h_act) cudaFreeHost(ctx->h_act);
+  if (ctx->h_flag) cudaFreeHost(ctx->h_flag);
   for (auto& t : ctx->pending) {
     cudaEventDestroy(t.e0);
     cudaEventDestroy(t.e1);
@@ -740,7 +1093,9 @@ ewh_status ewh_create(const ewh_grid_desc* desc, const double* rho, const double
          alloc_zero(&ctx->part, (size_t)ctx->nblk * nrhs) == cudaSuccess &&
          alloc_zero(&ctx->scal, (size_t)S_N * nrhs) == cudaSuccess &&
          alloc_zero(&ctx->active, nrhs) == cudaSuccess && alloc_zero(&ctx->flags, 1) == cudaSuccess &&
-         cudaMallocHost(&ctx->h_scal, sizeof(double) * S_N * nrhs) == cudaSuccess;
+         cudaMallocHost(&ctx->h_scal, sizeof(double) * S_N * nrhs) == cudaSuccess &&
+         cudaMallocHost(&ctx->h_act, sizeof(int) * nrhs) == cudaSuccess &&
+         cudaMallocHost(&ctx->h_flag, sizeof(int)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       s = fail(ctx, EWH_ENOMEM, "device allocation of the Krylov workspace failed");
@@ -779,6 +1134,8 @@ ewh_status ewh_get_info(const ewh_ctx* ctx, ewh_problem_info* info) {
   info->n_unknowns = (long long)ctx->g.dim * ctx->g.nodes;
   info->nrhs = ctx->g.nrhs;
   for (int a = 0; a < 3; ++a) info->nu[a] = ctx->g.nu[a];
+  info->kernel_variant[0] = ctx->w64.variant;
+  info->kernel_variant[1] = ctx->w32.variant;
   return EWH_OK;
 }
 
@@ -884,6 +1241,127 @@ ewh_status ewh_residual_history(const ewh_ctx* ctx, double* out, int cap, int* c
 }
 
 long long ewh_kernel_launches(const ewh_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+void ewh_batch_destroy(ewh_batch* b) {
+  if (!b) return;
+  if (b->master) cudaStreamSynchronize(b->master);
+  if (b->iter_graph) cudaGraphExecDestroy(b->iter_graph);
+  for (auto c : b->p) ewh_destroy(c);
+  for (auto e : b->joins) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->master) cudaStreamDestroy(b->master);
+  delete b;
+}
+
+ewh_status ewh_batch_create(const ewh_problem* probs, int nprob, void* cuda_stream, ewh_batch** out) {
+  if (!out) return fail(nullptr, EWH_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!probs || nprob < 1 || nprob > 4096) return fail(nullptr, EWH_EINVAL, "nprob must be in [1, 4096]");
+  for (int k = 1; k < nprob; ++k)
+    if (probs[k].desc.dim != probs[0].desc.dim || probs[k].desc.order != probs[0].desc.order ||
+        probs[k].desc.precision != probs[0].desc.precision)
+      return fail(nullptr, EWH_EINVAL, "batch members must share dim, order and precision");
+  ewh_batch* b = new ewh_batch();
+  b->user_stream = (cudaStream_t)cuda_stream;
+  b->precision = probs[0].desc.precision;
+  for (int k = 0; k < nprob; ++k) {
+    ewh_ctx* c = nullptr;
+    ewh_status s = ewh_create(&probs[k].desc, probs[k].rho, probs[k].lambda, probs[k].mu, probs[k].omega,
+                              probs[k].forcing, probs[k].nrhs, cuda_stream, &c);
+    if (s != EWH_OK) {
+      const std::string m = "member " + std::to_string(k) + ": " + g_create_error;
+      ewh_batch_destroy(b);
+      g_create_error = m;
+      return s;
+    }
+    b->p.push_back(c);
+  }
+  b->joins.resize(nprob, nullptr);
+  bool ok = cudaStreamCreateWithFlags(&b->master, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; ok && k < nprob; ++k)
+    ok = cudaEventCreateWithFlags(&b->joins[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    ewh_batch_destroy(b);
+    return fail(nullptr, EWH_ECUDA, "cannot create batch streams/events");
+  }
+  *out = b;
+  return EWH_OK;
+}
+
+ewh_status ewh_batch_member(ewh_batch* b, int k, ewh_ctx** ctx) {
+  if (!b || !ctx || k < 0 || k >= (int)b->p.size()) return EWH_EINVAL;
+  *ctx = b->p[k];
+  return EWH_OK;
+}
+
+long long ewh_batch_kernel_launches(const ewh_batch* b) {
+  if (!b) return 0;
+  long long n = b->launches;
+  for (auto c : b->p) n += c->launches;
+  return n;
+}
+
+const char* ewh_batch_last_error(const ewh_batch* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+ewh_status ewh_batch_apply_S(ewh_batch* b, const double* const* v_in, double* const* v_out) {
+  if (!b || !v_in || !v_out) return EWH_EINVAL;
+  std::vector<int> members;
+  for (int k = 0; k < (int)b->p.size(); ++k) {
+    members.push_back(k);
+    const ewh_status s0 = b->precision == EWH_FP64 ? ensure_graph<double>(b->p[k], false)
+                                                   : ensure_graph<float>(b->p[k], false);
+    if (s0 != EWH_OK) return bfail(b, s0, b->p[k]->err);
+  }
+  cudaEventRecord(b->fork, b->user_stream);
+  cudaStreamWaitEvent(b->master, b->fork, 0);
+  cudaGraphExec_t ge = nullptr;
+  auto body = [&](int k) -> ewh_status {
+    ewh_ctx* ctx = b->p[k];
+    if (b->precision == EWH_FP64) {
+      Wave<double>& w = ctx->w64;
+      if (launch_pack<double>(ctx->g, v_in[k], w.u_a, ctx->st) != cudaSuccess) return EWH_ECUDA;
+      long long cnt = 0;
+      if (enqueue_steps<double>(ctx, w, false, &cnt) != cudaSuccess) return EWH_ECUDA;
+      if (launch_unpack<double>(ctx->g, w.acc, v_out[k], nullptr, ctx->st) != cudaSuccess) return EWH_ECUDA;
+      b->launches += cnt + 2;
+    } else {
+      Wave<float>& w = ctx->w32;
+      if (launch_pack<float>(ctx->g, v_in[k], w.u_a, ctx->st) != cudaSuccess) return EWH_ECUDA;
+      long long cnt = 0;
+      if (enqueue_steps<float>(ctx, w, false, &cnt) != cudaSuccess) return EWH_ECUDA;
+      if (launch_unpack<float>(ctx->g, w.acc, v_out[k], nullptr, ctx->st) != cudaSuccess) return EWH_ECUDA;
+      b->launches += cnt + 2;
+    }
+    return EWH_OK;
+  };
+  ewh_status s = capture_branches(b, members, body, &ge);
+  if (s != EWH_OK) return s;
+  cudaError_t e = cudaGraphLaunch(ge, b->master);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->master);
+  cudaGraphExecDestroy(ge);
+  if (e != cudaSuccess) return bfail(b, EWH_ECUDA, std::string("batch apply failed: ") + cudaGetErrorString(e));
+  cudaEventRecord(b->fork, b->master);
+  cudaStreamWaitEvent(b->user_stream, b->fork, 0);
+  return EWH_OK;
+}
+
+ewh_status ewh_batch_solve(ewh_batch* b, double tol, int maxit, double* const* v_out, ewh_solve_info* infos) {
+  if (!b) return EWH_EINVAL;
+  if (!(tol > 0.0) || maxit < 0) return bfail(b, EWH_EINVAL, "tol must be > 0 and maxit >= 0");
+  for (auto c : b->p)
+    if (!c->has_forcing) return bfail(b, EWH_EINVAL, "every member needs forcing to be solved");
+  cudaEventRecord(b->fork, b->user_stream);
+  for (auto c : b->p) cudaStreamWaitEvent(c->st, b->fork, 0);
+  ewh_status s = b->precision == EWH_FP64 ? batch_solve_T<double>(b, tol, maxit, v_out, infos)
+                                          : batch_solve_T<float>(b, tol, maxit, v_out, infos);
+  for (auto c : b->p) {
+    cudaEventRecord(c->ev_out, c->st);
+    cudaStreamWaitEvent(b->user_stream, c->ev_out, 0);
+  }
+  return s;
+}
 
 ewh_status ewh_get_stats(ewh_ctx* ctx, ewh_stats* out) {
   if (!ctx || !out) return EWH_EINVAL;

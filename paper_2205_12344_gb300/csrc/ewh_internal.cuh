@@ -27,7 +27,15 @@ struct Geom {
   int off[3];      // full-grid index of the first unknown node per axis
   long long nodes; // unknown nodes per component
   int nrhs;
+  int variant;     // step-kernel variant chosen by the autotuner (host side)
 };
+
+// Number of step-kernel variants worth timing for a geometry/order.
+inline int step_variant_count(int dim, int order) {
+  if (dim == 2 && order == 4) return 2;  // split, fused
+  if (dim == 2 && order == 2) return 3;  // tile heights 8, 4, 16
+  return 1;
+}
 
 __host__ __device__ inline long long pidx(const Geom& g, int rhs, int comp, int x, int y, int z) {
   return ((long long)(rhs * g.dim + comp)) * g.field +

@@ -65,6 +65,14 @@ __device__ __forceinline__ T sbp_d1(const T* v, long long s, int p, int N) {
   return (v[-2 * s] - T(8) * v[-s] + T(8) * v[s] - v[2 * s]) * T(1.0 / 12.0);
 }
 
+// Programmatic dependent launch: a step kernel may start while the previous
+// one drains.  Before pdl_wait() a kernel reads only data the solve never
+// writes (lambda, mu, 1/(rho h^2), f/rho); pdl_wait() returns once the previous
+// kernel has completed and its writes are visible; pdl_trigger() lets the next
+// kernel begin launching.  Both are no-ops for a normal launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Time update shared by all kernels.  a = M^{-1} K u (FP of the state).
 // ---------------------------------------------------------------------------
@@ -96,10 +104,12 @@ __device__ __forceinline__ void leapfrog_update(const WaveFields<T>& f, long lon
 // ---------------------------------------------------------------------------
 // Order 2, 2D: 32 x 8 tile, one node per thread, halo 1 in shared memory.
 // ---------------------------------------------------------------------------
-template <typename T, int MODE, bool FORCED>
-__global__ void __launch_bounds__(256) step2d_o2(Geom g, WaveFields<T> f, StepScalars s) {
+template <typename T, int MODE, bool FORCED, int TYV>
+__global__ void __launch_bounds__(32 * TYV) step2d_o2(Geom g, WaveFields<T> f, StepScalars s) {
   if (g.dim != 2) return;
-  constexpr int TX = 32, TY = 8, SX = TX + 2, SY = TY + 2;
+  pdl_wait();
+  pdl_trigger();
+  constexpr int TX = 32, TY = TYV, SX = TX + 2, SY = TY + 2;
   __shared__ T su[2][SY][SX];
   __shared__ T sl[SY][SX];
   __shared__ T sm[SY][SX];
@@ -190,6 +200,8 @@ __global__ void __launch_bounds__(256) step2d_o2(Geom g, WaveFields<T> f, StepSc
 template <typename T, int MODE, bool FORCED>
 __global__ void __launch_bounds__(256) step3d_o2(Geom g, WaveFields<T> f, StepScalars s) {
   if (g.dim != 3) return;
+  pdl_wait();
+  pdl_trigger();
   constexpr int TX = 32, TY = 4, TZ = 2, SX = TX + 2, SY = TY + 2, SZ = TZ + 2;
   __shared__ T su[3][SZ][SY][SX];
   __shared__ T sl[SZ][SY][SX];
@@ -299,6 +311,8 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(256) sbp_stress(Geom g, const T* __restrict__ u, const T* __restrict__ lam,
                                                   const T* __restrict__ mu, T* __restrict__ sig) {
   if (g.dim != DIM) return;  // launched for the wrong dimension: touch nothing
+  pdl_wait();
+  pdl_trigger();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   int z = 0, rhs = blockIdx.z;
@@ -336,6 +350,8 @@ __global__ void __launch_bounds__(256) sbp_stress(Geom g, const T* __restrict__ 
 template <typename T, int DIM, int MODE, bool FORCED>
 __global__ void __launch_bounds__(256) sbp_divergence_step(Geom g, WaveFields<T> f, StepScalars s) {
   if (g.dim != DIM) return;
+  pdl_wait();
+  pdl_trigger();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   int z = 0, rhs = blockIdx.z;
@@ -368,6 +384,162 @@ __global__ void __launch_bounds__(256) sbp_divergence_step(Geom g, WaveFields<T>
 }
 
 // ---------------------------------------------------------------------------
+// Order 4 (SBP), 2D, split into two launches (stresses, then divergence and
+// update), one node per thread, 32 x 8 blocks.  Blocks whose nodes and stencil
+// reach lie inside the grid away from every SBP closure row stage their
+// operands (tile + 2-node halo) in shared memory with a few independent
+// coalesced loads per thread and difference them there; blocks near a side
+// run the generic per-node code from global memory.
+// ---------------------------------------------------------------------------
+constexpr int TL_TX = 32, TL_TY = 8, TL_H = 2;
+
+template <typename T>
+__device__ __forceinline__ T c4(T m2, T m1, T p1, T p2) {
+  return (m2 - T(8) * m1 + T(8) * p1 - p2) * T(1.0 / 12.0);
+}
+
+// every node of the block and its 2-node reach lies in rows/columns 4..N-5
+__device__ __forceinline__ bool tl_block_interior(const Geom& g, int x0, int y0) {
+  return x0 >= 4 && x0 + TL_TX - 1 <= g.n[0] - 5 && y0 >= 4 && y0 + TL_TY - 1 <= g.n[1] - 5;
+}
+
+template <typename T>
+__device__ __forceinline__ void stress2d_node(const Geom& g, const T* u, const T* lam, const T* mu, T* sig, int rhs,
+                                              int x, int y) {
+  const long long sy = g.np[0];
+  const T* U = u + pidx(g, rhs, 0, x, y, 0);
+  const T* V = U + g.field;
+  const T u_x = sbp_d1<T>(U, 1, x, g.n[0]);
+  const T u_y = sbp_d1<T>(U, sy, y, g.n[1]);
+  const T v_x = sbp_d1<T>(V, 1, x, g.n[0]);
+  const T v_y = sbp_d1<T>(V, sy, y, g.n[1]);
+  const long long pc = pidx(g, 0, 0, x, y, 0);
+  const T l = lam[pc], m = mu[pc];
+  const T div = u_x + v_y;
+  T* out = sig + (long long)rhs * 3 * g.field + pc;
+  out[0] = l * div + T(2) * m * u_x;
+  out[g.field] = l * div + T(2) * m * v_y;
+  out[2 * g.field] = m * (u_y + v_x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) sbp_stress2d_tl(Geom g, const T* __restrict__ u, const T* __restrict__ lam,
+                                                       const T* __restrict__ mu, T* __restrict__ sig) {
+  if (g.dim != 2) return;
+  constexpr int SX = TL_TX + 2 * TL_H, SY = TL_TY + 2 * TL_H;
+  __shared__ T su[2][SY][SX];
+  const int rhs = blockIdx.z;
+  const int x0 = blockIdx.x * TL_TX, y0 = blockIdx.y * TL_TY;
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  if (!tl_block_interior(g, x0, y0)) {           // uniform per block
+    pdl_wait();
+    pdl_trigger();
+    if (x < g.n[0] && y < g.n[1]) stress2d_node<T>(g, u, lam, mu, sig, rhs, x, y);
+    return;
+  }
+  const long long pc = pidx(g, 0, 0, x, y, 0);
+  const T l = lam[pc], m = mu[pc];               // static: read before the wait
+  pdl_wait();
+  pdl_trigger();
+  const T* U = u + pidx(g, rhs, 0, x0 - TL_H, y0 - TL_H, 0);
+  const int tid = threadIdx.y * TL_TX + threadIdx.x;
+  for (int i = tid; i < SX * SY; i += TL_TX * TL_TY) {
+    const int lx = i % SX, ly = i / SX;
+    const long long off = (long long)ly * g.np[0] + lx;
+    su[0][ly][lx] = U[off];
+    su[1][ly][lx] = U[off + g.field];
+  }
+  __syncthreads();
+  const int cx = threadIdx.x + TL_H, cy = threadIdx.y + TL_H;
+  const T u_x = c4(su[0][cy][cx - 2], su[0][cy][cx - 1], su[0][cy][cx + 1], su[0][cy][cx + 2]);
+  const T v_x = c4(su[1][cy][cx - 2], su[1][cy][cx - 1], su[1][cy][cx + 1], su[1][cy][cx + 2]);
+  const T u_y = c4(su[0][cy - 2][cx], su[0][cy - 1][cx], su[0][cy + 1][cx], su[0][cy + 2][cx]);
+  const T v_y = c4(su[1][cy - 2][cx], su[1][cy - 1][cx], su[1][cy + 1][cx], su[1][cy + 2][cx]);
+  const T div = u_x + v_y;
+  T* out = sig + (long long)rhs * 3 * g.field + pc;
+  out[0] = l * div + T(2) * m * u_x;
+  out[g.field] = l * div + T(2) * m * v_y;
+  out[2 * g.field] = m * (u_y + v_x);
+}
+
+template <typename T, int MODE, bool FORCED>
+__device__ __forceinline__ void div2d_node(const Geom& g, const WaveFields<T>& f, const StepScalars& s, int rhs, int x,
+                                           int y) {
+  if (!is_unknown(g, x, y, 0)) return;
+  const long long sy = g.np[0];
+  const long long pc = pidx(g, 0, 0, x, y, 0);
+  const T* sg = f.sigma + (long long)rhs * 3 * g.field + pc;
+  const T* sxx = sg;
+  const T* syy = sg + g.field;
+  const T* sxy = sg + 2 * g.field;
+  T ku = -sbp_d1<T>(sxx, 1, x, g.n[0]) - sbp_d1<T>(sxy, sy, y, g.n[1]);
+  T kv = -sbp_d1<T>(sxy, 1, x, g.n[0]) - sbp_d1<T>(syy, sy, y, g.n[1]);
+  const T inv_h0 = T(48.0 / 17.0);
+  if (x == 0) {
+    ku -= inv_h0 * sxx[0];
+    kv -= inv_h0 * sxy[0];
+  } else if (x == g.n[0] - 1) {
+    ku += inv_h0 * sxx[0];
+    kv += inv_h0 * sxy[0];
+  }
+  if (y == 0) {
+    ku -= inv_h0 * sxy[0];
+    kv -= inv_h0 * syy[0];
+  } else if (y == g.n[1] - 1) {
+    ku += inv_h0 * sxy[0];
+    kv += inv_h0 * syy[0];
+  }
+  const T irh = f.irh2[pc];
+  const long long p0 = pidx(g, rhs, 0, x, y, 0);
+  leapfrog_update<T, MODE, FORCED>(f, p0, f.u_cur[p0], ku * irh, s);
+  leapfrog_update<T, MODE, FORCED>(f, p0 + g.field, f.u_cur[p0 + g.field], kv * irh, s);
+}
+
+template <typename T, int MODE, bool FORCED>
+__global__ void __launch_bounds__(256) sbp_div2d_tl(Geom g, WaveFields<T> f, StepScalars s) {
+  if (g.dim != 2) return;
+  constexpr int SX = TL_TX + 2 * TL_H, SY = TL_TY + 2 * TL_H;
+  __shared__ T sxx[TL_TY][SX];   // x-halo only
+  __shared__ T syy[SY][TL_TX];   // y-halo only
+  __shared__ T sxy[SY][SX];      // both
+  const int rhs = blockIdx.z;
+  const int x0 = blockIdx.x * TL_TX, y0 = blockIdx.y * TL_TY;
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  if (!tl_block_interior(g, x0, y0)) {
+    pdl_wait();
+    pdl_trigger();
+    div2d_node<T, MODE, FORCED>(g, f, s, rhs, x, y);
+    return;
+  }
+  const long long pc = pidx(g, 0, 0, x, y, 0);
+  const long long p0 = pidx(g, rhs, 0, x, y, 0);
+  const T irh = f.irh2[pc];                       // static: read before the wait
+  pdl_wait();
+  pdl_trigger();
+  const T* base = f.sigma + (long long)rhs * 3 * g.field;
+  const T* Gxx = base + pidx(g, 0, 0, x0 - TL_H, y0, 0);
+  const T* Gyy = base + g.field + pidx(g, 0, 0, x0, y0 - TL_H, 0);
+  const T* Gxy = base + 2 * g.field + pidx(g, 0, 0, x0 - TL_H, y0 - TL_H, 0);
+  const int tid = threadIdx.y * TL_TX + threadIdx.x;
+  for (int i = tid; i < SX * SY; i += TL_TX * TL_TY) {
+    const int lx = i % SX, ly = i / SX;
+    sxy[ly][lx] = Gxy[(long long)ly * g.np[0] + lx];
+    if (ly < TL_TY) sxx[ly][lx] = Gxx[(long long)ly * g.np[0] + lx];
+    if (lx < TL_TX) syy[ly][lx] = Gyy[(long long)ly * g.np[0] + lx];
+  }
+  const T u0 = f.u_cur[p0], u1 = f.u_cur[p0 + g.field];
+  __syncthreads();
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int cx = tx + TL_H, cy = ty + TL_H;
+  const T ku = -c4(sxx[ty][cx - 2], sxx[ty][cx - 1], sxx[ty][cx + 1], sxx[ty][cx + 2]) -
+               c4(sxy[cy - 2][cx], sxy[cy - 1][cx], sxy[cy + 1][cx], sxy[cy + 2][cx]);
+  const T kv = -c4(sxy[cy][cx - 2], sxy[cy][cx - 1], sxy[cy][cx + 1], sxy[cy][cx + 2]) -
+               c4(syy[cy - 2][tx], syy[cy - 1][tx], syy[cy + 1][tx], syy[cy + 2][tx]);
+  leapfrog_update<T, MODE, FORCED>(f, p0, u0, ku * irh, s);
+  leapfrog_update<T, MODE, FORCED>(f, p0 + g.field, u1, kv * irh, s);
+}
+
+// ---------------------------------------------------------------------------
 // Order 4 (SBP), 2D, fused: one launch per time level.  A 32 x 16 tile (32 x 8
 // in FP64, to stay within 48 KB of static shared memory) stages
 // u on tile +- 6 nodes and lambda, mu on tile +- 3 in shared memory, forms the
@@ -380,6 +552,8 @@ __host__ __device__ constexpr int o4_tile_y() { return sizeof(T) == 8 ? 8 : 16; 
 template <typename T, int MODE, bool FORCED>
 __global__ void __launch_bounds__(512) step2d_o4_fused(Geom g, WaveFields<T> f, StepScalars s) {
   if (g.dim != 2) return;
+  pdl_wait();
+  pdl_trigger();
   constexpr int TX = 32, TY = o4_tile_y<T>(), HU = 6, HS = 3;
   constexpr int UX = TX + 2 * HU, UY = TY + 2 * HU;
   constexpr int SX = TX + 2 * HS, SY = TY + 2 * HS;
@@ -454,146 +628,39 @@ __global__ void __launch_bounds__(512) step2d_o4_fused(Geom g, WaveFields<T> f, 
 }
 
 // ---------------------------------------------------------------------------
-// Order 4 (SBP), 2D, streaming: one launch per time level.  A CTA of 32 x 8
-// threads owns a 32-node column strip of SROWS rows and walks down it 8 rows
-// at a time.  Shared-memory ring buffers of 16 rows hold u (x-halo 6) and the
-// stresses (x-halo 3); per 8 output rows it loads 8 new u rows, forms 8 new
-// stress rows (3 rows ahead) and updates the 8 rows.  Halo overhead is only in
-// x (44/32 u loads, 38/32 stresses) plus 9 rows per strip.
-// ---------------------------------------------------------------------------
-constexpr int ST_TX = 32, ST_TY = 8, ST_RING = 16, ST_HU = 6, ST_HS = 3;
-constexpr int ST_UX = ST_TX + 2 * ST_HU, ST_SX = ST_TX + 2 * ST_HS;
-constexpr int ST_SROWS = 64;
-
-// SBP first derivative along y on a ring of rows: row r lives in slot r & 15.
-template <typename T>
-__device__ __forceinline__ T sbp_d1_ring(const T* base, int row_stride, int q, int N) {
-  auto at = [&](int r) -> T { return base[(r & (ST_RING - 1)) * row_stride]; };
-  if (q < 4) {
-    T acc = T(0);
-#pragma unroll
-    for (int j = 0; j < 6; ++j) acc += sbp_coef<T>(q, j) * at(j);
-    return acc;
-  }
-  if (q > N - 5) {
-    const int r = N - 1 - q;
-    T acc = T(0);
-#pragma unroll
-    for (int j = 0; j < 6; ++j) acc -= sbp_coef<T>(r, j) * at(N - 1 - j);
-    return acc;
-  }
-  return (at(q - 2) - T(8) * at(q - 1) + T(8) * at(q + 1) - at(q + 2)) * T(1.0 / 12.0);
-}
-
-template <typename T, int MODE, bool FORCED>
-__global__ void __launch_bounds__(256) step2d_o4_stream(Geom g, WaveFields<T> f, StepScalars s) {
-  if (g.dim != 2) return;
-  __shared__ T ur[2][ST_RING][ST_UX];
-  __shared__ T sr[3][ST_RING][ST_SX];
-  const int rhs = blockIdx.z;
-  const int x0 = blockIdx.x * ST_TX;
-  const int ys = blockIdx.y * ST_SROWS;
-  const int nx = g.n[0], ny = g.n[1];
-  const int yend = min(ys + ST_SROWS, ny);  // output rows [ys, yend)
-  const int tid = threadIdx.y * ST_TX + threadIdx.x;
-  const long long comp_off = g.field;
-  const T* ubase = f.u_cur + (long long)(rhs * g.dim) * g.field;  // start of (rhs, comp 0)
-
-  // u rows [r0, r1) into the ring (zero outside the grid)
-  auto load_u = [&](int r0, int r1) {
-    const int cnt = (r1 - r0) * ST_UX;
-    for (int i = tid; i < cnt; i += ST_TX * ST_TY) {
-      const int lx = i % ST_UX, r = r0 + i / ST_UX;
-      T a = T(0), b = T(0);
-      if (r >= 0 && r < ny) {
-        const long long off = (long long)(r + PAD) * g.np[0] + (x0 - ST_HU + lx + PAD);
-        a = ubase[off];
-        b = ubase[off + comp_off];
-      }
-      ur[0][r & (ST_RING - 1)][lx] = a;
-      ur[1][r & (ST_RING - 1)][lx] = b;
-    }
-  };
-  // stress rows [q0, q1) from the u ring
-  auto stress = [&](int q0, int q1) {
-    const int cnt = (q1 - q0) * ST_SX;
-    for (int i = tid; i < cnt; i += ST_TX * ST_TY) {
-      const int lx = i % ST_SX, q = q0 + i / ST_SX;
-      const int qx = x0 - ST_HS + lx;
-      T sxx = T(0), syy = T(0), sxy = T(0);
-      if (q >= 0 && q < ny && qx >= 0 && qx < nx) {
-        const int ux = lx + (ST_HU - ST_HS);
-        const int slot = q & (ST_RING - 1);
-        const T u_x = sbp_d1<T>(&ur[0][slot][ux], 1, qx, nx);
-        const T v_x = sbp_d1<T>(&ur[1][slot][ux], 1, qx, nx);
-        const T u_y = sbp_d1_ring<T>(&ur[0][0][ux], ST_UX, q, ny);
-        const T v_y = sbp_d1_ring<T>(&ur[1][0][ux], ST_UX, q, ny);
-        const long long pc = pidx(g, 0, 0, qx, q, 0);
-        const T l = f.lam[pc], m = f.mu[pc];
-        const T div = u_x + v_y;
-        sxx = l * div + T(2) * m * u_x;
-        syy = l * div + T(2) * m * v_y;
-        sxy = m * (u_y + v_x);
-      }
-      const int slot = q & (ST_RING - 1);
-      sr[0][slot][lx] = sxx;
-      sr[1][slot][lx] = syy;
-      sr[2][slot][lx] = sxy;
-    }
-  };
-
-  // prologue: u rows [ys-6, ys+6), stresses [ys-3, ys+3)
-  load_u(ys - ST_HU, ys + ST_HU);
-  __syncthreads();
-  stress(ys - ST_HS, ys + ST_HS);
-  const T inv_h0 = T(48.0 / 17.0);
-  for (int j0 = ys; j0 < yend; j0 += ST_TY) {
-    load_u(j0 + ST_HU, j0 + ST_HU + ST_TY);        // u rows j0+6 .. j0+13
-    __syncthreads();
-    stress(j0 + ST_HS, j0 + ST_HS + ST_TY);        // stresses j0+3 .. j0+10
-    __syncthreads();
-    const int x = x0 + threadIdx.x, y = j0 + threadIdx.y;
-    if (y < yend && is_unknown(g, x, y, 0)) {
-      const int lx = threadIdx.x + ST_HS;
-      const int slot = y & (ST_RING - 1);
-      T ku = -sbp_d1<T>(&sr[0][slot][lx], 1, x, nx) - sbp_d1_ring<T>(&sr[2][0][lx], ST_SX, y, ny);
-      T kv = -sbp_d1<T>(&sr[2][slot][lx], 1, x, nx) - sbp_d1_ring<T>(&sr[1][0][lx], ST_SX, y, ny);
-      if (x == 0) {
-        ku -= inv_h0 * sr[0][slot][lx];
-        kv -= inv_h0 * sr[2][slot][lx];
-      } else if (x == nx - 1) {
-        ku += inv_h0 * sr[0][slot][lx];
-        kv += inv_h0 * sr[2][slot][lx];
-      }
-      if (y == 0) {
-        ku -= inv_h0 * sr[2][slot][lx];
-        kv -= inv_h0 * sr[1][slot][lx];
-      } else if (y == ny - 1) {
-        ku += inv_h0 * sr[2][slot][lx];
-        kv += inv_h0 * sr[1][slot][lx];
-      }
-      const T irh = f.irh2[pidx(g, 0, 0, x, y, 0)];
-      const long long p0 = pidx(g, rhs, 0, x, y, 0);
-      leapfrog_update<T, MODE, FORCED>(f, p0, f.u_cur[p0], ku * irh, s);
-      leapfrog_update<T, MODE, FORCED>(f, p0 + g.field, f.u_cur[p0 + g.field], kv * irh, s);
-    }
-    // the next iteration overwrites stress slots of rows j0-5 .. j0+2, read above
-    __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-// 2D order-4 kernel variant: 0 = stress + divergence launches (default,
-// measured faster on GB300), 1 = single fused launch.  EWH_STEP2D_O4=fused
-// selects the latter; it is read whenever launches are enqueued (a context
-// captures its step graph once, on first use).
-static int step2d_o4_variant() {
+// Launch with programmatic stream serialization (see pdl_wait); EWH_PDL=0
+// turns it off.
+static bool pdl_enabled() {
+  const char* e = getenv("EWH_PDL");
+  return !(e && e[0] == '0');
+}
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// 2D order-4 kernel variant: 0 = stress + divergence launches, 1 = single
+// fused launch.  Chosen per context by the autotuner (Geom::variant);
+// EWH_STEP2D_O4=fused|split overrides it (read whenever launches are
+// enqueued; a context captures its step graph once, on first use).
+static int step2d_o4_variant(const Geom& g) {
   const char* e = getenv("EWH_STEP2D_O4");
   if (e && e[0] == 'f') return 1;
-  if (e && e[0] == 's' && e[1] == 't') return 2;
-  return 0;
+  if (e && e[0] == 's') return 0;
+  return g.variant == 1 ? 1 : 0;
 }
 
 template <typename T, int MODE, bool FORCED>
@@ -601,36 +668,43 @@ static cudaError_t launch_mode(const Geom& g, int order, const WaveFields<T>& f,
                                cudaStream_t st, long long* nl) {
   if (order == 2) {
     if (g.dim == 2) {
-      dim3 blk(32, 8), grd((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.nrhs);
-      step2d_o2<T, MODE, FORCED><<<grd, blk, 0, st>>>(g, f, s);
+      // tile height chosen per context (autotuner): 0 -> 8, 1 -> 4, 2 -> 16 rows
+      const int ty = g.variant == 1 ? 4 : (g.variant == 2 ? 16 : 8);
+      dim3 blk(32, ty), grd((g.n[0] + 31) / 32, (g.n[1] + ty - 1) / ty, g.nrhs);
+      cudaError_t e = ty == 4    ? launch_k(step2d_o2<T, MODE, FORCED, 4>, grd, blk, st, g, f, s)
+                      : ty == 16 ? launch_k(step2d_o2<T, MODE, FORCED, 16>, grd, blk, st, g, f, s)
+                                 : launch_k(step2d_o2<T, MODE, FORCED, 8>, grd, blk, st, g, f, s);
+      if (e != cudaSuccess) return e;
     } else {
       dim3 blk(32, 4, 2), grd((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, ((g.n[2] + 1) / 2) * g.nrhs);
-      step3d_o2<T, MODE, FORCED><<<grd, blk, 0, st>>>(g, f, s);
+      cudaError_t e = launch_k(step3d_o2<T, MODE, FORCED>, grd, blk, st, g, f, s);
+      if (e != cudaSuccess) return e;
     }
     if (nl) *nl += 1;
     return cudaGetLastError();
   }
-  if (g.dim == 2 && step2d_o4_variant() == 2) {
-    dim3 blk(ST_TX, ST_TY), grd((g.n[0] + ST_TX - 1) / ST_TX, (g.n[1] + ST_SROWS - 1) / ST_SROWS, g.nrhs);
-    step2d_o4_stream<T, MODE, FORCED><<<grd, blk, 0, st>>>(g, f, s);
-    if (nl) *nl += 1;
-    return cudaGetLastError();
-  }
-  if (g.dim == 2 && step2d_o4_variant() == 1) {
+  if (g.dim == 2 && step2d_o4_variant(g) == 1) {
     constexpr int TY = o4_tile_y<T>();
     dim3 blk(32, TY), grd((g.n[0] + 31) / 32, (g.n[1] + TY - 1) / TY, g.nrhs);
-    step2d_o4_fused<T, MODE, FORCED><<<grd, blk, 0, st>>>(g, f, s);
+    cudaError_t e = launch_k(step2d_o4_fused<T, MODE, FORCED>, grd, blk, st, g, f, s);
+    if (e != cudaSuccess) return e;
     if (nl) *nl += 1;
     return cudaGetLastError();
   }
   dim3 blk(32, 8);
   dim3 grd((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.dim == 2 ? g.nrhs : g.n[2] * g.nrhs);
   if (g.dim == 2) {
-    sbp_stress<T, 2><<<grd, blk, 0, st>>>(g, f.u_cur, f.lam, f.mu, f.sigma);
-    sbp_divergence_step<T, 2, MODE, FORCED><<<grd, blk, 0, st>>>(g, f, s);
+    dim3 tgrd((g.n[0] + TL_TX - 1) / TL_TX, (g.n[1] + TL_TY - 1) / TL_TY, g.nrhs);
+    cudaError_t e = launch_k(sbp_stress2d_tl<T>, tgrd, dim3(TL_TX, TL_TY), st, g, (const T*)f.u_cur, f.lam, f.mu,
+                             f.sigma);
+    if (e != cudaSuccess) return e;
+    e = launch_k(sbp_div2d_tl<T, MODE, FORCED>, tgrd, dim3(TL_TX, TL_TY), st, g, f, s);
+    if (e != cudaSuccess) return e;
   } else {
-    sbp_stress<T, 3><<<grd, blk, 0, st>>>(g, f.u_cur, f.lam, f.mu, f.sigma);
-    sbp_divergence_step<T, 3, MODE, FORCED><<<grd, blk, 0, st>>>(g, f, s);
+    cudaError_t e = launch_k(sbp_stress<T, 3>, grd, blk, st, g, (const T*)f.u_cur, f.lam, f.mu, f.sigma);
+    if (e != cudaSuccess) return e;
+    e = launch_k(sbp_divergence_step<T, 3, MODE, FORCED>, grd, blk, st, g, f, s);
+    if (e != cudaSuccess) return e;
   }
   if (nl) *nl += 2;
   return cudaGetLastError();
