@@ -320,6 +320,12 @@ ewh_status ewh_slice_channels(const float* dy, float* dx, long long P, int C, in
 /* FP32 -> BF16 conversion of n values. */
 ewh_status ewh_f32_to_bf16(const float* a, void* b, long long n, void* stream);
 
+/* Per-sample scaled L2 loss of FP32 y [N][P][C] (first Cu channels) against
+ * FP32 t [N][P][Cu]: loss[n] = 1/2 ||y_n - t_n||^2 / ||t_n||^2; grad = d(mean
+ * loss)/dy (zero on channels >= Cu). */
+ewh_status ewh_scaled_l2_loss(const float* y, const float* t, float* grad, float* loss, long long P, int C, int Cu,
+                              int N, void* stream);
+
 /* One Adam step (Kingma and Ba 2015, bias-corrected, step >= 1) on FP32
  * parameters; param_bf16 (may be NULL) receives the updated BF16 copy. */
 ewh_status ewh_adam_step(float* param, const float* grad, float* m, float* v, void* param_bf16, long long n,

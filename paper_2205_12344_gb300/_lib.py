@@ -72,6 +72,28 @@ SIGNATURES = {
     "ewh_batch_kernel_launches": (ctypes.c_longlong, [_P]),
     "ewh_batch_last_error": (ctypes.c_char_p, [_P]),
     "ewh_batch_destroy": (None, [_P]),
+    "ewh_conv3x3_fwd": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int, _P]),
+    "ewh_conv3x3_dgrad": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, _P]),
+    "ewh_conv3x3_wgrad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, _P]),
+    "ewh_bias_grad": (ctypes.c_int, [_P, _P, ctypes.c_longlong, ctypes.c_int, _P]),
+    "ewh_leaky_relu_bwd": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_longlong, _P]),
+    "ewh_avgpool2": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    "ewh_avgpool2_bwd": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    "ewh_upsample2": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, _P]),
+    "ewh_upsample2_bwd": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, _P]),
+    "ewh_copy_channels": (ctypes.c_int, [_P, _P, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    "ewh_slice_channels": (ctypes.c_int, [_P, _P, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, _P]),
+    "ewh_f32_to_bf16": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P]),
+    "ewh_scaled_l2_loss": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_longlong, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, _P]),
+    "ewh_adam_step": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_longlong, ctypes.c_float, ctypes.c_float,
+                                     ctypes.c_float, ctypes.c_float, ctypes.c_int, _P]),
     "ewh_destroy": (None, [_P]),
     "ewh_last_error": (ctypes.c_char_p, [_P]),
     "ewh_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -261,3 +283,75 @@ def ewh_destroy(ctx):
 
 def ewh_last_error(ctx=None):
     return load().ewh_last_error(ctx).decode()
+
+
+# ---- warm-start layers (device tensors; stream = torch stream handle or None)
+
+def _s(stream):
+    return ctypes.c_void_p(stream) if stream else None
+
+
+def _net(name, *args):
+    st = load()
+    fn = getattr(st, name)
+    conv = []
+    for a in args:
+        conv.append(_ptr(a) if (a is not None and hasattr(a, "data_ptr")) else a)
+    return _check(fn(*conv))
+
+
+def ewh_conv3x3_fwd(x, w, bias, y_pre, y_act, act, N, H, W, Ci, Co, stream=None):
+    return _net("ewh_conv3x3_fwd", x, w, bias, y_pre, y_act, int(act), N, H, W, Ci, Co, _s(stream))
+
+
+def ewh_conv3x3_dgrad(dy, w, w_scratch, dx, N, H, W, Ci, Co, stream=None):
+    return _net("ewh_conv3x3_dgrad", dy, w, w_scratch, dx, N, H, W, Ci, Co, _s(stream))
+
+
+def ewh_conv3x3_wgrad(x, dy, dw, N, H, W, Ci, Co, stream=None):
+    return _net("ewh_conv3x3_wgrad", x, dy, dw, N, H, W, Ci, Co, _s(stream))
+
+
+def ewh_bias_grad(dy, db, P, C, stream=None):
+    return _net("ewh_bias_grad", dy, db, P, C, _s(stream))
+
+
+def ewh_leaky_relu_bwd(pre, dy, dx, dx_bf16, n, stream=None):
+    return _net("ewh_leaky_relu_bwd", pre, dy, dx, dx_bf16, n, _s(stream))
+
+
+def ewh_avgpool2(x, y, N, H, W, C, stream=None):
+    return _net("ewh_avgpool2", x, y, N, H, W, C, _s(stream))
+
+
+def ewh_avgpool2_bwd(dy, dx, N, H, W, C, stream=None):
+    return _net("ewh_avgpool2_bwd", dy, dx, N, H, W, C, _s(stream))
+
+
+def ewh_upsample2(x, y, N, H, W, C, Cy, c_off, stream=None):
+    return _net("ewh_upsample2", x, y, N, H, W, C, Cy, c_off, _s(stream))
+
+
+def ewh_upsample2_bwd(dy, dx, N, H, W, C, Cy, c_off, stream=None):
+    return _net("ewh_upsample2_bwd", dy, dx, N, H, W, C, Cy, c_off, _s(stream))
+
+
+def ewh_copy_channels(x, y, P, C, Cy, c_off, stream=None):
+    return _net("ewh_copy_channels", x, y, P, C, Cy, c_off, _s(stream))
+
+
+def ewh_slice_channels(dy, dx, P, C, Cy, c_off, accumulate, stream=None):
+    return _net("ewh_slice_channels", dy, dx, P, C, Cy, c_off, int(accumulate), _s(stream))
+
+
+def ewh_f32_to_bf16(a, b, n, stream=None):
+    return _net("ewh_f32_to_bf16", a, b, n, _s(stream))
+
+
+def ewh_adam_step(param, grad, m, v, param_bf16, n, lr, beta1, beta2, eps, step, stream=None):
+    return _net("ewh_adam_step", param, grad, m, v, param_bf16, n, float(lr), float(beta1), float(beta2),
+                float(eps), int(step), _s(stream))
+
+
+def ewh_scaled_l2_loss(y, t, grad, loss, P, C, Cu, N, stream=None):
+    return _net("ewh_scaled_l2_loss", y, t, grad, loss, P, C, Cu, N, _s(stream))

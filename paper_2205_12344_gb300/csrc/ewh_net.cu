@@ -311,6 +311,40 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
   }
 }
 
+// Per-sample scaled L2 loss on the first `cu` of `c` channels:
+//   loss_s = 1/2 ||y_s - t_s||^2 / ||t_s||^2,  grad = (y - t) / (||t_s||^2 * nsamp)
+// (t is FP32 [N][P][cu], y FP32 [N][P][c]); one block per sample.
+__global__ void scaled_l2_kernel(const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ grad,
+                                 float* __restrict__ loss, long long P, int c, int cu, int nsamp) {
+  __shared__ float s_tt[256], s_dd[256];
+  const int n = blockIdx.x;
+  const float* yn = y + (long long)n * P * c;
+  const float* tn = t + (long long)n * P * cu;
+  float tt = 0.f, dd = 0.f;
+  for (long long i = threadIdx.x; i < P * cu; i += 256) {
+    const float d = yn[(i / cu) * c + (i % cu)] - tn[i];
+    tt += tn[i] * tn[i];
+    dd += d * d;
+  }
+  s_tt[threadIdx.x] = tt;
+  s_dd[threadIdx.x] = dd;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s_tt[threadIdx.x] += s_tt[threadIdx.x + o];
+      s_dd[threadIdx.x] += s_dd[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  const float inv = 1.f / fmaxf(s_tt[0], 1e-30f);
+  if (threadIdx.x == 0) loss[n] = 0.5f * s_dd[0] * inv;
+  float* gn = grad + (long long)n * P * c;
+  for (long long i = threadIdx.x; i < P * c; i += 256) {
+    const int ch = (int)(i % c);
+    gn[i] = ch < cu ? (yn[i] - tn[(i / c) * cu + ch]) * inv / nsamp : 0.f;
+  }
+}
+
 int egrid(long long n) {
   long long b = (n + 255) / 256;
   if (b > 4096) b = 4096;
@@ -427,6 +461,13 @@ ewh_status ewh_slice_channels(const float* dy, float* dx, long long P, int C, in
 ewh_status ewh_f32_to_bf16(const float* a, void* b, long long n, void* stream) {
   if (!a || !b || n < 0) return nfail("ewh_f32_to_bf16: bad arguments");
   f32_to_bf16_kernel<<<egrid(n), 256, 0, (cudaStream_t)stream>>>(a, (bf16*)b, n);
+  return launched();
+}
+
+ewh_status ewh_scaled_l2_loss(const float* y, const float* t, float* grad, float* loss, long long P, int C, int Cu,
+                              int N, void* stream) {
+  if (!y || !t || !grad || !loss || P < 1 || Cu < 1 || Cu > C || N < 1) return nfail("ewh_scaled_l2_loss: bad arguments");
+  scaled_l2_kernel<<<N, 256, 0, (cudaStream_t)stream>>>(y, t, grad, loss, P, C, Cu, N);
   return launched();
 }
 
