@@ -163,6 +163,15 @@ ewh_status ewh_mdot(ewh_ctx* ctx, const double* x, const double* y, double* out)
 ewh_status ewh_solve(ewh_ctx* ctx, double tol, int maxit, const double* x0_or_null,
                      double* v_out, ewh_solve_info* info);
 
+/* Same problem and stopping rule as ewh_solve, by the conjugate residual
+ * method in the M inner product (Section 4.5, remark on conjugate residual:
+ * the residual norm is non-increasing, which the paper prefers for sweeps over
+ * w).  One S apply per iteration (on the residual); in the FP32-stencil
+ * precision the residual is replaced by the FP64 true residual each time it
+ * has fallen tenfold, restarting the directions from it. */
+ewh_status ewh_solve_cr(ewh_ctx* ctx, double tol, int maxit, const double* x0_or_null, double* v_out,
+                        ewh_solve_info* info);
+
 /* Copy up to cap entries of the last solve's residual history (relative
  * M-norm of the recursive residual after each iteration, max over rhs) to the
  * host array out; returns the number of entries available via *count. */

@@ -416,6 +416,45 @@ def cg_solve(s: System, tol=1e-8, maxit=10000, x0=None, rhs: int = 0, b=None):
     return x, info
 
 
+def cr_solve(s: System, tol=1e-8, maxit=10000, x0=None, rhs: int = 0, b=None):
+    """Conjugate residual in the M inner product on (I - S) v = b (Section 4.5
+    remark: the residual norm does not increase).  One S apply per iteration."""
+    if b is None:
+        b = apply_Pi0(s, rhs)
+
+    def A(v):
+        return v - apply_S(s, v, rhs)
+
+    bb = math.sqrt(mdot(s, b, b))
+    info = SolveInfo()
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    r = b - A(x) if x0 is not None else b.copy()
+    info.history.append(math.sqrt(mdot(s, r, r)) / bb)
+    if info.history[-1] <= tol:
+        info.converged, info.rel_res = True, info.history[-1]
+        return x, info
+    Ar = A(r)
+    p, Ap = r.copy(), Ar.copy()
+    rAr = mdot(s, r, Ar)
+    for it in range(1, maxit + 1):
+        alpha = rAr / mdot(s, Ap, Ap)
+        x = x + alpha * p
+        r = r - alpha * Ap
+        info.history.append(math.sqrt(mdot(s, r, r)) / bb)
+        info.iters = it
+        if info.history[-1] <= tol:
+            info.converged = True
+            break
+        Ar = A(r)
+        rAr_new = mdot(s, r, Ar)
+        beta = rAr_new / rAr
+        rAr = rAr_new
+        p = r + beta * p
+        Ap = Ar + beta * Ap
+    info.rel_res = info.history[-1]
+    return x, info
+
+
 def helmholtz_direct(s: System, rhs: int = 0):
     """Definition-level solution: (w_eff^2 M - K) v = W f with w_eff = w for
     the corrected scheme and w~ for the standard one (Section 4.3)."""

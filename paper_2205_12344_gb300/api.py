@@ -86,6 +86,13 @@ class WaveHoltz:
         info = L.ewh_solve(self.ctx, tol, maxit, x0v, out, raise_on_error=raise_on_error)
         return out, info
 
+    def solve_cr(self, tol=1e-8, maxit=100000, x0=None, raise_on_error=True):
+        """Conjugate residual instead of CG (non-increasing residual)."""
+        out = self._vec()
+        x0v = self._vec(x0) if x0 is not None else None
+        info = L.ewh_solve_cr(self.ctx, tol, maxit, x0v, out, raise_on_error=raise_on_error)
+        return out, info
+
     def residual_history(self):
         return L.ewh_residual_history(self.ctx)
 

@@ -38,7 +38,7 @@ struct Wave {
   long long graph_S_kernels = 0;
   long long graph_Pi0_kernels = 0;
   int variant = -1;           // step-kernel variant (autotuner), -1 = not chosen yet
-  float variant_ms[4] = {0, 0, 0, 0};
+  float variant_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   bool ready = false;
 };
 
@@ -62,6 +62,7 @@ struct ewh_ctx {
   // Krylov state (FP64): x, r, p, q, b, d (correction), tmp
   double *kx = nullptr, *kr = nullptr, *kp = nullptr, *kq = nullptr, *kb = nullptr, *kd = nullptr,
          *ktmp = nullptr;
+  double *kar = nullptr, *kap = nullptr;  // conjugate residual: A r, A p
   double* mw = nullptr;     // mass weight per unknown node
   double* part = nullptr;   // reduction partials [nrhs][nblk]
   double* scal = nullptr;   // per rhs: rr, alpha, beta, bb, res, dot  (6 * nrhs)
@@ -264,7 +265,7 @@ std::string tune_key(const ewh_ctx* ctx) {
   for (auto& ch : name)
     if (ch == '"' || ch == ' ') ch = '_';
   const Geom& g = ctx->g;
-  return name + "|d" + std::to_string(g.dim) + "|o" + std::to_string(ctx->order) + "|" +
+  return name + "|v2|d" + std::to_string(g.dim) + "|o" + std::to_string(ctx->order) + "|" +
          (sizeof(T) == 8 ? "f64" : "f32") + "|" + std::to_string(g.n[0]) + "x" + std::to_string(g.n[1]) + "x" +
          std::to_string(g.n[2]) + "|r" + std::to_string(g.nrhs);
 }
@@ -317,7 +318,7 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
     float ms = 1e30f;
     if (ok && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
     cudaGetLastError();
-    if (v < 4) w.variant_ms[v] = ms;
+    if (v < 8) w.variant_ms[v] = ms;
     if (ms < best_ms) {
       best_ms = ms;
       best = v;
@@ -673,8 +674,134 @@ ewh_status run_cg(ewh_ctx* ctx, double* x, double* r, double tol, int maxit, dou
   return EWH_OK;
 }
 
+// Conjugate residual in the M inner product (the paper's choice for its FD
+// sweeps: the residual norm never increases).  On entry x is the iterate and
+// r its true FP64 residual; one S apply (precision T) per iteration:
+//   alpha = (r, Ar)/(Ap, Ap); x += alpha p; r -= alpha Ap; Ar = A r;
+//   beta = (r, Ar)_new/(r, Ar)_old; p = r + beta p; Ap = Ar + beta Ap.
+// When the recursive residual reaches tol (or, for FP32, falls tenfold since
+// the last check) r is replaced by the FP64 true residual and the direction
+// set restarts from it (p = r, Ap = A r); convergence is declared on the true
+// residual only.
+template <typename T>
+ewh_status ar_apply(ewh_ctx* ctx, double* src, double* dst) {
+  Wave<T>& w = wave_of<T>(ctx);
+  EWH_CU(launch_pack<T>(ctx->g, src, w.u_a, ctx->st));
+  EWH_CU(launch_timed_graph<T>(ctx, w.graph_S));
+  EWH_CU(launch_unpack<T>(ctx->g, w.acc, dst, src, ctx->st));  // dst = src - S src
+  ctx->launches += 2 + w.graph_S_kernels;
+  return EWH_OK;
+}
+
+template <typename T>
+ewh_status cr_restart(ewh_ctx* ctx, double* r, ewh_solve_info* inf) {
+  const long long n = total_unknowns(ctx);
+  ewh_status st = ar_apply<T>(ctx, r, ctx->kar);
+  if (st != EWH_OK) return st;
+  if (sizeof(T) == 8) ++inf->s_applies_fp64;
+  else ++inf->s_applies;
+  EWH_CU(cudaMemcpyAsync(ctx->kp, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->st));
+  EWH_CU(cudaMemcpyAsync(ctx->kap, ctx->kar, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->st));
+  EWH_CU(launch_mdot_partial(ctx->g, ctx->mw, r, ctx->kar, ctx->part, ctx->st));
+  EWH_CU(launch_cr_beta(ctx->g.nrhs, ctx->part, ctx->nblk, sc(ctx, S_DOT), sc(ctx, S_BETA), ctx->active, 1, ctx->st));
+  ctx->launches += 2;
+  return EWH_OK;
+}
+
+template <typename T>
+ewh_status run_cr(ewh_ctx* ctx, double* x, double* r, double tol, int maxit, double drop, ewh_solve_info* inf,
+                  double* rel_out) {
+  const Geom& g = ctx->g;
+  const int R = g.nrhs;
+  ewh_status st = ensure_graph<T>(ctx, false);
+  if (st != EWH_OK) return st;
+  // true residual norms and active mask
+  st = mdot_dev(ctx, r, r, sc(ctx, S_RR));
+  if (st != EWH_OK) return st;
+  EWH_CU(cudaMemsetAsync(ctx->flags, 0, sizeof(int), ctx->st));
+  EWH_CU(cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * S_N * R, cudaMemcpyDeviceToHost, ctx->st));
+  EWH_CU(cudaStreamSynchronize(ctx->st));
+  std::vector<double> true_res(R), anchor(R);
+  bool any = false;
+  for (int k = 0; k < R; ++k) {
+    true_res[k] = anchor[k] = std::sqrt(ctx->h_scal[S_RR * R + k] / ctx->h_scal[S_BB * R + k]);
+    ctx->h_act[k] = true_res[k] > tol;
+    any = any || ctx->h_act[k];
+  }
+  EWH_CU(cudaMemcpyAsync(ctx->active, ctx->h_act, sizeof(int) * R, cudaMemcpyHostToDevice, ctx->st));
+  auto worst = [&]() {
+    double m = 0.0;
+    for (double v : true_res) m = std::max(m, v);
+    return m;
+  };
+  ctx->history.push_back(worst());
+  if (any) {
+    st = cr_restart<T>(ctx, r, inf);
+    if (st != EWH_OK) return st;
+  }
+  while (any && inf->iters < maxit) {
+    // alpha = (r, Ar) / (Ap, Ap)      (S_DOT holds (r, Ar))
+    EWH_CU(launch_mdot_partial(g, ctx->mw, ctx->kap, ctx->kap, ctx->part, ctx->st));
+    EWH_CU(launch_cg_alpha(R, ctx->part, ctx->nblk, sc(ctx, S_DOT), sc(ctx, S_ALPHA), ctx->active, ctx->flags,
+                           ctx->st));
+    // x += alpha p ; r -= alpha Ap ; res = ||r||_M / ||b||_M
+    EWH_CU(launch_cg_xr_update(g, ctx->mw, sc(ctx, S_ALPHA), ctx->kp, ctx->kap, x, r, ctx->part, ctx->st));
+    EWH_CU(launch_res(R, ctx->part, ctx->nblk, sc(ctx, S_BB), sc(ctx, S_RES), ctx->active, ctx->st));
+    ctx->launches += 4;
+    // Ar = A r ; beta ; p, Ap
+    st = ar_apply<T>(ctx, r, ctx->kar);
+    if (st != EWH_OK) return st;
+    EWH_CU(launch_mdot_partial(g, ctx->mw, r, ctx->kar, ctx->part, ctx->st));
+    EWH_CU(launch_cr_beta(R, ctx->part, ctx->nblk, sc(ctx, S_DOT), sc(ctx, S_BETA), ctx->active, 0, ctx->st));
+    EWH_CU(launch_cr_pupdate(g, r, ctx->kar, ctx->kp, ctx->kap, sc(ctx, S_BETA), ctx->st));
+    ctx->launches += 3;
+    ++inf->iters;
+    if (sizeof(T) == 8) ++inf->s_applies_fp64;
+    else ++inf->s_applies;
+    EWH_CU(cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * S_N * R, cudaMemcpyDeviceToHost, ctx->st));
+    EWH_CU(cudaMemcpyAsync(ctx->h_flag, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    EWH_CU(cudaStreamSynchronize(ctx->st));
+    if (*ctx->h_flag & 1) {
+      *rel_out = worst();
+      return fail(ctx, EWH_EBREAKDOWN, "CR breakdown: (Ap, Ap)_M <= 0");
+    }
+    bool replace = false;
+    double hist = 0.0;
+    for (int k = 0; k < R; ++k) {
+      if (!ctx->h_act[k]) continue;
+      const double res = ctx->h_scal[S_RES * R + k];
+      hist = std::max(hist, res);
+      if (res <= tol || (drop > 0.0 && res <= drop * anchor[k])) replace = true;
+    }
+    ctx->history.push_back(hist);
+    if (replace) {
+      double dummy = 0.0;
+      st = true_residual(ctx, x, r, &dummy);
+      if (st != EWH_OK) return st;
+      ++inf->s_applies_fp64;
+      bool changed = false;
+      any = false;
+      for (int k = 0; k < R; ++k) {
+        true_res[k] = anchor[k] = std::sqrt(ctx->h_scal[S_DOT * R + k] / ctx->h_scal[S_BB * R + k]);
+        if (ctx->h_act[k] && true_res[k] <= tol) {
+          ctx->h_act[k] = 0;
+          changed = true;
+        }
+        any = any || ctx->h_act[k];
+      }
+      if (changed) EWH_CU(cudaMemcpyAsync(ctx->active, ctx->h_act, sizeof(int) * R, cudaMemcpyHostToDevice, ctx->st));
+      if (any) {
+        st = cr_restart<T>(ctx, r, inf);
+        if (st != EWH_OK) return st;
+      }
+    }
+  }
+  *rel_out = worst();
+  return EWH_OK;
+}
+
 ewh_status solve_impl(ewh_ctx* ctx, double tol, int maxit, const double* x0, double* v_out,
-                      ewh_solve_info* inf) {
+                      ewh_solve_info* inf, int method = 0) {
   const Geom& g = ctx->g;
   const long long n = total_unknowns(ctx);
   ctx->history.clear();
@@ -700,7 +827,10 @@ ewh_status solve_impl(ewh_ctx* ctx, double tol, int maxit, const double* x0, dou
   // every time the recursive residual fell tenfold, so the FP32 operator's
   // rounding never accumulates in the residual beyond one decade.
   ewh_status result;
-  if (ctx->precision == EWH_FP64) {
+  if (method == 1) {
+    result = ctx->precision == EWH_FP64 ? run_cr<double>(ctx, ctx->kx, ctx->kr, tol, maxit, 0.0, inf, &rel)
+                                        : run_cr<float>(ctx, ctx->kx, ctx->kr, tol, maxit, 0.1, inf, &rel);
+  } else if (ctx->precision == EWH_FP64) {
     result = run_cg<double>(ctx, ctx->kx, ctx->kr, tol, maxit, 0.0, inf, &rel);
   } else {
     result = run_cg<float>(ctx, ctx->kx, ctx->kr, tol, maxit, 0.1, inf, &rel);
@@ -935,6 +1065,8 @@ void ewh_destroy(ewh_ctx* ctx) {
   cudaFree(ctx->kb);
   cudaFree(ctx->kd);
   cudaFree(ctx->ktmp);
+  cudaFree(ctx->kar);
+  cudaFree(ctx->kap);
   cudaFree(ctx->mw);
   cudaFree(ctx->part);
   cudaFree(ctx->scal);
@@ -1090,6 +1222,7 @@ ewh_status ewh_create(const ewh_grid_desc* desc, const double* rho, const double
          alloc_zero(&ctx->kp, n) == cudaSuccess && alloc_zero(&ctx->kq, n) == cudaSuccess &&
          alloc_zero(&ctx->kb, n) == cudaSuccess && alloc_zero(&ctx->kd, n) == cudaSuccess &&
          alloc_zero(&ctx->ktmp, n) == cudaSuccess && alloc_zero(&ctx->mw, g.nodes) == cudaSuccess &&
+         alloc_zero(&ctx->kar, n) == cudaSuccess && alloc_zero(&ctx->kap, n) == cudaSuccess &&
          alloc_zero(&ctx->part, (size_t)ctx->nblk * nrhs) == cudaSuccess &&
          alloc_zero(&ctx->scal, (size_t)S_N * nrhs) == cudaSuccess &&
          alloc_zero(&ctx->active, nrhs) == cudaSuccess && alloc_zero(&ctx->flags, 1) == cudaSuccess &&
@@ -1223,6 +1356,26 @@ ewh_status ewh_solve(ewh_ctx* ctx, double tol, int maxit, const double* x0_or_nu
   enter(ctx);
   ewh_solve_info inf{};
   s = solve_impl(ctx, tol, maxit, x0_or_null, v_out, &inf);
+  leave(ctx);
+  cudaStreamSynchronize(ctx->st);
+  inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  inf.status = s;
+  if (info) *info = inf;
+  if (s == EWH_OK) s = check_async(ctx);
+  return s;
+}
+
+ewh_status ewh_solve_cr(ewh_ctx* ctx, double tol, int maxit, const double* x0_or_null, double* v_out,
+                        ewh_solve_info* info) {
+  if (!ctx || !v_out) return fail(ctx, EWH_EINVAL, "null argument");
+  if (!(tol > 0.0) || maxit < 0) return fail(ctx, EWH_EINVAL, "tol must be > 0 and maxit >= 0");
+  if (!ctx->has_forcing) return fail(ctx, EWH_EINVAL, "problem was created without forcing");
+  ewh_status s = check_async(ctx);
+  if (s != EWH_OK) return s;
+  const auto t0 = std::chrono::steady_clock::now();
+  enter(ctx);
+  ewh_solve_info inf{};
+  s = solve_impl(ctx, tol, maxit, x0_or_null, v_out, &inf, 1);
   leave(ctx);
   cudaStreamSynchronize(ctx->st);
   inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

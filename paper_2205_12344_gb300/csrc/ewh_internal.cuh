@@ -32,7 +32,7 @@ struct Geom {
 
 // Number of step-kernel variants worth timing for a geometry/order.
 inline int step_variant_count(int dim, int order) {
-  if (dim == 2 && order == 4) return 2;  // split, fused
+  if (dim == 2 && order == 4) return 5;  // split with 4 block shapes, fused
   if (dim == 2 && order == 2) return 3;  // tile heights 8, 4, 16
   return 1;
 }
@@ -120,6 +120,14 @@ cudaError_t launch_cg_beta(int nrhs, const double* part, int nblk, double* rr, c
 //   after a residual replacement: beta *= dot / rr ; rr = dot ; res = sqrt(dot / bb)
 cudaError_t launch_cg_replace(int nrhs, const double* dot, double* rr, double* beta, double* res, const double* bb,
                               cudaStream_t st);
+// conjugate residual: res = sqrt((r,r)_M / bb); beta = (r,Ar)_new/(r,Ar)_old;
+// p = r + beta p, Ap = Ar + beta Ap
+cudaError_t launch_res(int nrhs, const double* part, int nblk, const double* bb, double* res, const int* active,
+                       cudaStream_t st);
+cudaError_t launch_cr_beta(int nrhs, const double* part, int nblk, double* rar, double* beta, const int* active,
+                           int init, cudaStream_t st);
+cudaError_t launch_cr_pupdate(const Geom& g, const double* r, const double* ar, double* p, double* ap,
+                              const double* beta, cudaStream_t st);
 cudaError_t launch_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t st);
 cudaError_t launch_fill_mass(const Geom& g, int order, const double* rho_full, double h, double* mw,
                              cudaStream_t st);

@@ -236,6 +236,58 @@ cudaError_t launch_cg_replace(int nrhs, const double* dot, double* rr, double* b
   return cudaGetLastError();
 }
 
+// ---- conjugate residual pieces ---------------------------------------------
+// res = sqrt((r, r)_M / bb) from the partial sums of (r, r)_M
+__global__ void res_kernel(const double* __restrict__ part, int nblk, const double* __restrict__ bb,
+                           double* __restrict__ res, const int* __restrict__ active) {
+  const int rhs = blockIdx.x;
+  const double rn = sum_partials(part + (long long)rhs * nblk, nblk);
+  if (threadIdx.x == 0 && active[rhs]) res[rhs] = sqrt(rn / bb[rhs]);
+}
+// beta = (r, Ar)_new / (r, Ar)_old ; (r, Ar) = new   (sets it when init != 0)
+__global__ void cr_beta_kernel(const double* __restrict__ part, int nblk, double* __restrict__ rar,
+                               double* __restrict__ beta, const int* __restrict__ active, int init) {
+  const int rhs = blockIdx.x;
+  const double v = sum_partials(part + (long long)rhs * nblk, nblk);
+  if (threadIdx.x == 0) {
+    if (init) {
+      rar[rhs] = v;
+      beta[rhs] = 0.0;
+    } else if (active[rhs]) {
+      beta[rhs] = rar[rhs] != 0.0 ? v / rar[rhs] : 0.0;
+      rar[rhs] = v;
+    } else {
+      beta[rhs] = 0.0;
+    }
+  }
+}
+// p = r + beta p ; Ap = Ar + beta Ap
+__global__ void cr_pupdate_kernel(Geom g, const double* __restrict__ r, const double* __restrict__ ar,
+                                  double* __restrict__ p, double* __restrict__ ap, const double* __restrict__ beta) {
+  const long long n = (long long)g.dim * g.nodes;
+  const long long total = n * g.nrhs;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const double b = beta[i / n];
+    p[i] = r[i] + b * p[i];
+    ap[i] = ar[i] + b * ap[i];
+  }
+}
+cudaError_t launch_res(int nrhs, const double* part, int nblk, const double* bb, double* res, const int* active,
+                       cudaStream_t st) {
+  res_kernel<<<nrhs, RED_THREADS, 0, st>>>(part, nblk, bb, res, active);
+  return cudaGetLastError();
+}
+cudaError_t launch_cr_beta(int nrhs, const double* part, int nblk, double* rar, double* beta, const int* active,
+                           int init, cudaStream_t st) {
+  cr_beta_kernel<<<nrhs, RED_THREADS, 0, st>>>(part, nblk, rar, beta, active, init);
+  return cudaGetLastError();
+}
+cudaError_t launch_cr_pupdate(const Geom& g, const double* r, const double* ar, double* p, double* ap,
+                              const double* beta, cudaStream_t st) {
+  cr_pupdate_kernel<<<grid_for((long long)g.dim * g.nodes * g.nrhs), 256, 0, st>>>(g, r, ar, p, ap, beta);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cg_alpha(int nrhs, const double* pq_part, int nblk, const double* rr, double* alpha, int* active,
                             int* flags, cudaStream_t st) {
   cg_alpha_kernel<<<nrhs, RED_THREADS, 0, st>>>(pq_part, nblk, rr, alpha, active, flags);

@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(256) sbp_divergence_step(Geom g, WaveFields<T>
 // coalesced loads per thread and difference them there; blocks near a side
 // run the generic per-node code from global memory.
 // ---------------------------------------------------------------------------
-constexpr int TL_TX = 32, TL_TY = 8, TL_H = 2;
+constexpr int TL_H = 2;
 
 template <typename T>
 __device__ __forceinline__ T c4(T m2, T m1, T p1, T p2) {
@@ -399,6 +399,7 @@ __device__ __forceinline__ T c4(T m2, T m1, T p1, T p2) {
 }
 
 // every node of the block and its 2-node reach lies in rows/columns 4..N-5
+template <int TL_TX, int TL_TY>
 __device__ __forceinline__ bool tl_block_interior(const Geom& g, int x0, int y0) {
   return x0 >= 4 && x0 + TL_TX - 1 <= g.n[0] - 5 && y0 >= 4 && y0 + TL_TY - 1 <= g.n[1] - 5;
 }
@@ -422,16 +423,17 @@ __device__ __forceinline__ void stress2d_node(const Geom& g, const T* u, const T
   out[2 * g.field] = m * (u_y + v_x);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) sbp_stress2d_tl(Geom g, const T* __restrict__ u, const T* __restrict__ lam,
-                                                       const T* __restrict__ mu, T* __restrict__ sig) {
+template <typename T, int TL_TX, int TL_TY>
+__global__ void __launch_bounds__(TL_TX * TL_TY) sbp_stress2d_tl(Geom g, const T* __restrict__ u,
+                                                                 const T* __restrict__ lam, const T* __restrict__ mu,
+                                                                 T* __restrict__ sig) {
   if (g.dim != 2) return;
   constexpr int SX = TL_TX + 2 * TL_H, SY = TL_TY + 2 * TL_H;
   __shared__ T su[2][SY][SX];
   const int rhs = blockIdx.z;
   const int x0 = blockIdx.x * TL_TX, y0 = blockIdx.y * TL_TY;
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-  if (!tl_block_interior(g, x0, y0)) {           // uniform per block
+  if (!tl_block_interior<TL_TX, TL_TY>(g, x0, y0)) {  // uniform per block
     pdl_wait();
     pdl_trigger();
     if (x < g.n[0] && y < g.n[1]) stress2d_node<T>(g, u, lam, mu, sig, rhs, x, y);
@@ -495,8 +497,8 @@ __device__ __forceinline__ void div2d_node(const Geom& g, const WaveFields<T>& f
   leapfrog_update<T, MODE, FORCED>(f, p0 + g.field, f.u_cur[p0 + g.field], kv * irh, s);
 }
 
-template <typename T, int MODE, bool FORCED>
-__global__ void __launch_bounds__(256) sbp_div2d_tl(Geom g, WaveFields<T> f, StepScalars s) {
+template <typename T, int MODE, bool FORCED, int TL_TX, int TL_TY>
+__global__ void __launch_bounds__(TL_TX * TL_TY) sbp_div2d_tl(Geom g, WaveFields<T> f, StepScalars s) {
   if (g.dim != 2) return;
   constexpr int SX = TL_TX + 2 * TL_H, SY = TL_TY + 2 * TL_H;
   __shared__ T sxx[TL_TY][SX];   // x-halo only
@@ -505,7 +507,7 @@ __global__ void __launch_bounds__(256) sbp_div2d_tl(Geom g, WaveFields<T> f, Ste
   const int rhs = blockIdx.z;
   const int x0 = blockIdx.x * TL_TX, y0 = blockIdx.y * TL_TY;
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-  if (!tl_block_interior(g, x0, y0)) {
+  if (!tl_block_interior<TL_TX, TL_TY>(g, x0, y0)) {
     pdl_wait();
     pdl_trigger();
     div2d_node<T, MODE, FORCED>(g, f, s, rhs, x, y);
@@ -652,15 +654,30 @@ static cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cud
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-// 2D order-4 kernel variant: 0 = stress + divergence launches, 1 = single
-// fused launch.  Chosen per context by the autotuner (Geom::variant);
-// EWH_STEP2D_O4=fused|split overrides it (read whenever launches are
-// enqueued; a context captures its step graph once, on first use).
+// 2D order-4 kernel variants (Geom::variant, chosen per context by the
+// autotuner): 0..3 = stress + divergence launches with 32x8, 32x16, 64x8 or
+// 64x4 blocks, 4 = single fused launch.  EWH_STEP2D_O4=fused|split overrides
+// it (read whenever launches are enqueued; a context captures its step graph
+// once, on first use).
 static int step2d_o4_variant(const Geom& g) {
   const char* e = getenv("EWH_STEP2D_O4");
   if (e && e[0] == 'f') return 1;
   if (e && e[0] == 's') return 0;
-  return g.variant == 1 ? 1 : 0;
+  return g.variant == 4 ? 1 : 0;
+}
+static int step2d_o4_tile(const Geom& g) {
+  const char* e = getenv("EWH_STEP2D_O4");
+  if (e && e[0] == 's') return 0;
+  return (g.variant >= 0 && g.variant <= 3) ? g.variant : 0;
+}
+
+template <typename T, int MODE, bool FORCED, int TX, int TY>
+static cudaError_t launch_split_o4(const Geom& g, const WaveFields<T>& f, const StepScalars& s, cudaStream_t st) {
+  dim3 tgrd((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, g.nrhs);
+  cudaError_t e = launch_k(sbp_stress2d_tl<T, TX, TY>, tgrd, dim3(TX, TY), st, g, (const T*)f.u_cur, f.lam, f.mu,
+                           f.sigma);
+  if (e != cudaSuccess) return e;
+  return launch_k(sbp_div2d_tl<T, MODE, FORCED, TX, TY>, tgrd, dim3(TX, TY), st, g, f, s);
 }
 
 template <typename T, int MODE, bool FORCED>
@@ -694,11 +711,11 @@ static cudaError_t launch_mode(const Geom& g, int order, const WaveFields<T>& f,
   dim3 blk(32, 8);
   dim3 grd((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.dim == 2 ? g.nrhs : g.n[2] * g.nrhs);
   if (g.dim == 2) {
-    dim3 tgrd((g.n[0] + TL_TX - 1) / TL_TX, (g.n[1] + TL_TY - 1) / TL_TY, g.nrhs);
-    cudaError_t e = launch_k(sbp_stress2d_tl<T>, tgrd, dim3(TL_TX, TL_TY), st, g, (const T*)f.u_cur, f.lam, f.mu,
-                             f.sigma);
-    if (e != cudaSuccess) return e;
-    e = launch_k(sbp_div2d_tl<T, MODE, FORCED>, tgrd, dim3(TL_TX, TL_TY), st, g, f, s);
+    const int tv = step2d_o4_tile(g);
+    cudaError_t e = tv == 1   ? launch_split_o4<T, MODE, FORCED, 32, 16>(g, f, s, st)
+                    : tv == 2 ? launch_split_o4<T, MODE, FORCED, 64, 8>(g, f, s, st)
+                    : tv == 3 ? launch_split_o4<T, MODE, FORCED, 64, 4>(g, f, s, st)
+                              : launch_split_o4<T, MODE, FORCED, 32, 8>(g, f, s, st);
     if (e != cudaSuccess) return e;
   } else {
     cudaError_t e = launch_k(sbp_stress<T, 3>, grd, blk, st, g, (const T*)f.u_cur, f.lam, f.mu, f.sigma);

@@ -278,3 +278,24 @@ def test_order4_2d_kernel_variants_match_oracle(variant, shape, monkeypatch):
     with _wh(p, "fp32") as wh:
         assert rel_err(to_np(wh.apply_S(v)), want) < tol32(s.nt)
     assert kinds > 0
+
+
+def test_conjugate_residual_matches_oracle():
+    """ewh_solve_cr (FP64) follows the oracle's conjugate residual iterates and
+    reaches the direct solution; the FP32-stencil variant meets the FP64
+    residual tolerance."""
+    p = inputs.cfg_homogeneous_2d(nu=32, omega=10.0)
+    s = O.build_system(p)
+    xo, io = O.cr_solve(s, tol=1e-9)
+    v = O.helmholtz_direct(s)
+    with _wh(p) as wh:
+        x, info = wh.solve_cr(tol=1e-9)
+        hist = wh.residual_history()
+    assert info.status == 0 and abs(info.iters - io.iters) <= 1
+    n = min(15, len(hist), len(io.history))
+    assert np.allclose(hist[:n], io.history[:n], rtol=1e-7, atol=0)
+    assert rel_err(to_np(x), xo) < 1e-6
+    assert np.linalg.norm(to_np(x) - v) <= 1e-6 * np.linalg.norm(v)
+    with _wh(p, "fp32") as wh:
+        x32, i32 = wh.solve_cr(tol=1e-8)
+    assert i32.status == 0 and i32.rel_res <= 1e-8

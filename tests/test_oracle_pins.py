@@ -504,3 +504,15 @@ def test_window_helper_matches_full_apply():
         got = window_sample(p, s.nt, v, node, reach=4)
         want = np.array([full[c * nn + idx[node[1], node[0]]] for c in range(2)])
         assert np.abs(got - want).max() <= 1e-12 * np.abs(full).max()
+
+
+def test_conjugate_residual_converges_monotonically():
+    """Section 4.5 remark: conjugate residual (M inner product) reaches the
+    direct solution and its residual norm never increases (unlike CG's)."""
+    s = O.build_system(_case(2, 4, [0, 0, 0, 1], 1, seed=3))
+    v = O.helmholtz_direct(s)
+    x, info = O.cr_solve(s, tol=1e-11, maxit=500)
+    assert info.converged
+    assert np.linalg.norm(x - v) <= 1e-8 * np.linalg.norm(v)
+    h = np.array(info.history)
+    assert np.all(np.diff(h) <= 1e-12 * h[0])
