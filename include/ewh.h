@@ -69,7 +69,9 @@ enum {
 typedef struct {
   int dim;        /* 2 or 3 */
   int n[3];       /* nodes per axis including the two boundary nodes (>= 4;
-                     >= 8 for order 4) */
+                     >= 8 for order 4; each axis is stored padded to a
+                     multiple of 32 plus 12, and one padded component must
+                     hold fewer than 2^31 nodes) */
   double h;       /* grid spacing (> 0) */
   int order;      /* 2 or 4 */
   int bc[6];      /* EWH_BC_DIRICHLET or EWH_BC_FREE per side */

@@ -3,6 +3,8 @@
 // M (I - S) v = M Pi 0 (Section 4.5, eq. amat_sym).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <sys/stat.h>
 #include <unistd.h>
 
@@ -38,9 +40,20 @@ struct Wave {
   long long graph_S_kernels = 0;
   long long graph_Pi0_kernels = 0;
   int variant = -1;           // step-kernel variant (autotuner), -1 = not chosen yet
-  float variant_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int fallback = 0;           // fastest variant that is not the resident solve
+  float variant_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // per time level
   bool ready = false;
+  // on-chip resident solve (2D order 4 FP32, one rhs): per-level scalars,
+  // barrier words and the partition per CTA shape
+  double* d_cosn = nullptr;
+  double* d_wnew = nullptr;
+  unsigned* bar = nullptr;
+  ResidentPlan rplan[RS_SHAPES];
 };
+
+// step-kernel variants of the 2D order-4 FP32 solve beyond the launcher's
+// own (split tiles 0..3, fused 4): 5 + shape = resident solve of that shape
+constexpr int VARIANT_RESIDENT = 5;
 
 }  // namespace
 
@@ -73,6 +86,7 @@ struct ewh_ctx {
   int* h_flag = nullptr;    // pinned host mirror of flags
   int nblk = 1;
   long long launches = 0;
+  bool allow_resident = true;  // false for batch members (their branches run concurrently)
   std::string err = "no error";
   std::vector<double> history;
   // device timing of wave solves: pending event pairs, reusable events
@@ -168,6 +182,20 @@ ewh_status build_wave(ewh_ctx* ctx, Wave<T>& w, const double* d_rho, const doubl
       }
   }
   EWH_CU(cudaGetLastError());
+  if (sizeof(T) == 4 && g.dim == 2 && ctx->order == 4 && g.nrhs == 1) {
+    const int N = ctx->nt * ctx->periods;
+    std::vector<double> hc(N), hw(N);
+    for (int n = 0; n < N; ++n) {  // the same values as the per-level launches get
+      hc[n] = std::cos(2.0 * M_PI * (double)(n % ctx->nt) / (double)ctx->nt);
+      hw[n] = ctx->weights[n + 1];
+    }
+    EWH_CU(cudaMalloc(&w.d_cosn, sizeof(double) * N));
+    EWH_CU(cudaMalloc(&w.d_wnew, sizeof(double) * N));
+    EWH_CU(alloc_zero(&w.bar, 2));
+    EWH_CU(cudaMemcpy(w.d_cosn, hc.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+    EWH_CU(cudaMemcpy(w.d_wnew, hw.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+    for (int k = 0; k < RS_SHAPES; ++k) w.rplan[k] = plan_resident_o4(g, k);
+  }
   return EWH_OK;
 }
 
@@ -184,6 +212,9 @@ void free_wave(Wave<T>& w) {
   cudaFree(w.irh2);
   cudaFree(w.frho);
   cudaFree(w.sigma);
+  cudaFree(w.d_cosn);
+  cudaFree(w.d_wnew);
+  cudaFree(w.bar);
   w = Wave<T>();
 }
 
@@ -265,14 +296,68 @@ std::string tune_key(const ewh_ctx* ctx) {
   for (auto& ch : name)
     if (ch == '"' || ch == ' ') ch = '_';
   const Geom& g = ctx->g;
-  return name + "|v2|d" + std::to_string(g.dim) + "|o" + std::to_string(ctx->order) + "|" +
+  return name + "|v3" + (ctx->allow_resident ? "" : "b") + "|d" + std::to_string(g.dim) + "|o" + std::to_string(ctx->order) + "|" +
          (sizeof(T) == 8 ? "f64" : "f32") + "|" + std::to_string(g.n[0]) + "x" + std::to_string(g.n[1]) + "x" +
          std::to_string(g.n[2]) + "|r" + std::to_string(g.nrhs);
 }
 
+// Resident variant v usable by this context?  (FP32 2D order 4, one rhs,
+// a partition that fits on chip, not a batch member, EWH_RESIDENT != 0.)
+template <typename T>
+bool resident_ok(const ewh_ctx* ctx, const Wave<T>& w, int v) {
+  if (sizeof(T) != 4 || v < VARIANT_RESIDENT || v >= VARIANT_RESIDENT + RS_SHAPES || !ctx->allow_resident)
+    return false;
+  const char* e = getenv("EWH_RESIDENT");
+  if (e && e[0] == '0') return false;
+  return w.rplan[v - VARIANT_RESIDENT].ok != 0;
+}
+
+// One cooperative launch running nsteps levels of the wave solve on chip.
+template <typename T>
+cudaError_t enqueue_resident(ewh_ctx* ctx, Wave<T>& w, int v, bool forced, int nsteps) {
+  if constexpr (std::is_same<T, float>::value) {
+    ResidentIO io{};
+    io.u0 = w.u_a;
+    io.xbuf0 = w.u_b;
+    io.xbuf1 = w.delta;
+    io.acc = w.acc;
+    io.lam = w.lam;
+    io.mu = w.mu;
+    io.irh2 = w.irh2;
+    io.frho = forced ? w.frho : nullptr;
+    io.cosn = w.d_cosn;
+    io.wnew = w.d_wnew;
+    io.kt = ctx->kt;
+    io.w0 = ctx->weights[0];
+    io.nsteps = nsteps;
+    io.bar = w.bar;
+    return launch_resident_o4(ctx->g, w.rplan[v - VARIANT_RESIDENT], io, ctx->st);
+  } else {
+    (void)ctx;
+    (void)w;
+    (void)v;
+    (void)forced;
+    (void)nsteps;
+    return cudaErrorInvalidValue;
+  }
+}
+
 template <typename T>
 void autotune(ewh_ctx* ctx, Wave<T>& w) {
-  const int nv = step_variant_count(ctx->g.dim, ctx->order);
+  const int nbase = step_variant_count(ctx->g.dim, ctx->order);
+  const char* force = getenv("EWH_STEP2D_O4");
+  const bool forced_launcher = force && (force[0] == 's' || force[0] == 'f');
+  bool any_res = false;
+  for (int k = 0; k < RS_SHAPES && !forced_launcher; ++k) any_res |= resident_ok<T>(ctx, w, VARIANT_RESIDENT + k);
+  const int nv = any_res ? VARIANT_RESIDENT + RS_SHAPES : nbase;
+  w.fallback = 0;
+  if (force && force[0] == 'r') {  // EWH_STEP2D_O4=r, r0, r1, r2: resident solve of that CTA shape
+    const int k = (force[1] >= '0' && force[1] < '0' + RS_SHAPES) ? force[1] - '0' : 0;
+    if (resident_ok<T>(ctx, w, VARIANT_RESIDENT + k)) {
+      w.variant = VARIANT_RESIDENT + k;
+      return;
+    }
+  }
   const char* off = getenv("EWH_AUTOTUNE");
   if (nv <= 1 || (off && off[0] == '0')) {
     w.variant = 0;
@@ -282,7 +367,8 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
   const std::string key = tune_key<T>(ctx);
   auto cache = read_tune_cache(path);
   for (auto& kv : cache)
-    if (kv.first == key && kv.second >= 0 && kv.second < nv) {
+    if (kv.first == key && kv.second >= 0 && kv.second < nv &&
+        (kv.second < VARIANT_RESIDENT || resident_ok<T>(ctx, w, kv.second))) {
       w.variant = kv.second;
       return;
     }
@@ -303,24 +389,45 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
     w.variant = 0;
     return;
   }
-  int best = 0;
-  float best_ms = 1e30f;
+  int best = 0, best_base = 0;
+  float best_ms = 1e30f, best_base_ms = 1e30f;
+  const int N = ctx->nt * ctx->periods;
   for (int v = 0; v < nv; ++v) {
-    Geom g = ctx->g;
-    g.variant = v;
-    bool ok = true;
-    for (int k = 0; k < 10 && ok; ++k) {
-      if (k == 2) cudaEventRecord(e0, ctx->st);
-      ok = launch_step<T>(g, ctx->order, f, STEP_MID, sc, ctx->st, nullptr) == cudaSuccess;
-      std::swap(f.u_cur, f.u_next);
+    float per_level = 1e30f;
+    if (v >= VARIANT_RESIDENT) {
+      if (resident_ok<T>(ctx, w, v)) {
+        const int ns = std::min(N, 40);
+        bool ok = enqueue_resident<T>(ctx, w, v, false, std::min(N, 8)) == cudaSuccess;  // warm-up
+        cudaEventRecord(e0, ctx->st);
+        ok = ok && enqueue_resident<T>(ctx, w, v, false, ns) == cudaSuccess;
+        cudaEventRecord(e1, ctx->st);
+        float ms = 1e30f;
+        if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+          per_level = ms / ns;
+        cudaGetLastError();
+      }
+    } else if (v < nbase) {
+      Geom g = ctx->g;
+      g.variant = v;
+      bool ok = true;
+      for (int k = 0; k < 10 && ok; ++k) {
+        if (k == 2) cudaEventRecord(e0, ctx->st);
+        ok = launch_step<T>(g, ctx->order, f, STEP_MID, sc, ctx->st, nullptr) == cudaSuccess;
+        std::swap(f.u_cur, f.u_next);
+      }
+      cudaEventRecord(e1, ctx->st);
+      float ms = 1e30f;
+      if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+        per_level = ms / 8;
+      cudaGetLastError();
+      if (per_level < best_base_ms) {
+        best_base_ms = per_level;
+        best_base = v;
+      }
     }
-    cudaEventRecord(e1, ctx->st);
-    float ms = 1e30f;
-    if (ok && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-    cudaGetLastError();
-    if (v < 8) w.variant_ms[v] = ms;
-    if (ms < best_ms) {
-      best_ms = ms;
+    if (v < 8) w.variant_ms[v] = per_level;
+    if (per_level < best_ms) {
+      best_ms = per_level;
       best = v;
     }
   }
@@ -333,6 +440,12 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
   cudaMemsetAsync(w.delta, 0, sizeof(T) * state, ctx->st);
   cudaMemsetAsync(w.acc, 0, sizeof(T) * state, ctx->st);
   w.variant = best;
+  w.fallback = best_base;
+  if (getenv("EWH_VERBOSE")) {
+    fprintf(stderr, "ewh: autotune %s:", key.c_str());
+    for (int v = 0; v < nv && v < 8; ++v) fprintf(stderr, " v%d=%.4g", v, w.variant_ms[v]);
+    fprintf(stderr, " ms/level -> %d\n", best);
+  }
   cache.emplace_back(key, best);
   write_tune_cache(path, cache);
 }
@@ -341,6 +454,11 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
 template <typename T>
 cudaError_t enqueue_steps(ewh_ctx* ctx, Wave<T>& w, bool forced, long long* nl) {
   const int N = ctx->nt * ctx->periods;
+  if (w.variant >= VARIANT_RESIDENT) {  // all levels in one cooperative launch
+    cudaError_t e = enqueue_resident<T>(ctx, w, w.variant, forced, N);
+    if (e == cudaSuccess && nl) *nl += 1;
+    return e;
+  }
   Geom gv = ctx->g;
   gv.variant = w.variant < 0 ? 0 : w.variant;
   WaveFields<T> f{};
@@ -374,21 +492,29 @@ ewh_status ensure_graph(ewh_ctx* ctx, bool forced) {
   long long& nk = forced ? w.graph_Pi0_kernels : w.graph_S_kernels;
   if (ge) return EWH_OK;
   if (w.variant < 0) autotune<T>(ctx, w);
-  cudaGraph_t graph = nullptr;
-  EWH_CU(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
-  long long count = 0;
-  cudaError_t e = enqueue_steps<T>(ctx, w, forced, &count);
-  cudaError_t e2 = cudaStreamEndCapture(ctx->st, &graph);
-  if (e != cudaSuccess || e2 != cudaSuccess) {
+  for (int attempt = 0;; ++attempt) {
+    cudaGraph_t graph = nullptr;
+    EWH_CU(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+    long long count = 0;
+    cudaError_t e = enqueue_steps<T>(ctx, w, forced, &count);
+    cudaError_t e2 = cudaStreamEndCapture(ctx->st, &graph);
+    if (e == cudaSuccess && e2 == cudaSuccess) {
+      e = cudaGraphInstantiate(&ge, graph, 0);
+      e2 = cudaSuccess;
+    }
     if (graph) cudaGraphDestroy(graph);
-    return fail(ctx, EWH_ECUDA, std::string("graph capture failed: ") +
-                                    cudaGetErrorString(e != cudaSuccess ? e : e2));
+    if (e == cudaSuccess && e2 == cudaSuccess) {
+      nk = count;
+      return EWH_OK;
+    }
+    ge = nullptr;
+    cudaGetLastError();
+    if (attempt == 0 && w.variant >= VARIANT_RESIDENT) {  // not capturable here: per-level launches
+      w.variant = w.fallback;
+      continue;
+    }
+    return fail(ctx, EWH_ECUDA, std::string("graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
   }
-  e = cudaGraphInstantiate(&ge, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return fail(ctx, EWH_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-  nk = count;
-  return EWH_OK;
 }
 
 cudaEvent_t take_event(ewh_ctx* ctx) {
@@ -865,6 +991,11 @@ ewh_status validate_desc(const ewh_grid_desc* d, int nrhs) {
   for (int a = 0; a < d->dim; ++a)
     if (d->n[a] < minn || d->n[a] > (1 << 20))
       return fail(nullptr, EWH_EINVAL, "n[" + std::to_string(a) + "] must be in [" + std::to_string(minn) + ", 2^20]");
+  {  // one padded component must index in 32 bits (the step kernels use int offsets)
+    long long cells = 1;
+    for (int a = 0; a < d->dim; ++a) cells *= ((d->n[a] + TILE_ROUND - 1) / TILE_ROUND) * TILE_ROUND + 2 * PAD;
+    if (cells >= (1LL << 31)) return fail(nullptr, EWH_EINVAL, "grid too large: a padded component must hold < 2^31 nodes");
+  }
   for (int k = 0; k < 2 * d->dim; ++k)
     if (d->bc[k] != EWH_BC_DIRICHLET && d->bc[k] != EWH_BC_FREE)
       return fail(nullptr, EWH_EINVAL, "bc entries must be EWH_BC_DIRICHLET or EWH_BC_FREE");
@@ -1427,6 +1558,7 @@ ewh_status ewh_batch_create(const ewh_problem* probs, int nprob, void* cuda_stre
       g_create_error = m;
       return s;
     }
+    c->allow_resident = false;  // member solves run as concurrent graph branches
     b->p.push_back(c);
   }
   b->joins.resize(nprob, nullptr);

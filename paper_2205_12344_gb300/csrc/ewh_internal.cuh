@@ -132,6 +132,42 @@ cudaError_t launch_axpby(long long n, double a, const double* x, double b, doubl
 cudaError_t launch_fill_mass(const Geom& g, int order, const double* rho_full, double h, double* mw,
                              cudaStream_t st);
 
+// ---- on-chip resident wave solve (ewh_stencil.cu) --------------------------
+// Order 4 (SBP), 2D, FP32, one right-hand side: all nt*periods time levels in
+// one cooperative launch, one CTA per SM, each owning a bx x by block of
+// nodes whose state stays in shared memory and registers.  Shapes: threads
+// per CTA x own nodes per thread at most.
+constexpr int RS_SHAPES = 3;
+constexpr int RS_SHAPE_THREADS[RS_SHAPES] = {1024, 768, 512};
+constexpr int RS_SHAPE_NODES[RS_SHAPES] = {7, 9, 14};
+struct ResidentPlan {
+  int ok = 0;
+  int shape = 0;       // index into RS_SHAPE_*
+  int px = 0, py = 0;  // CTAs per axis
+  int bx = 0, by = 0;  // node block per CTA (the last block per axis may be smaller, >= 8)
+  size_t smem = 0;     // dynamic shared memory per CTA in bytes
+};
+// Partition of g for the current device and a CTA shape (ok = 0 when g does
+// not fit on chip).
+ResidentPlan plan_resident_o4(const Geom& g, int shape);
+struct ResidentIO {
+  const float* u0;      // u^0 (padded, 2 components)
+  float* xbuf0;         // exchange buffers for the rims of u (padded, 2 components)
+  float* xbuf1;
+  float* acc;           // filter accumulator, written at the end (unknowns only)
+  const float* lam;
+  const float* mu;
+  const float* irh2;
+  const float* frho;    // null: unforced
+  const double* cosn;   // [nsteps] cos(w t_n)
+  const double* wnew;   // [nsteps] trapezoid weight of level n+1
+  double kt;            // c dt^2
+  double w0;            // trapezoid weight of level 0
+  int nsteps;
+  unsigned* bar;        // [2] grid-barrier arrivals and error flag (zeroed by the launcher)
+};
+cudaError_t launch_resident_o4(const Geom& g, const ResidentPlan& p, const ResidentIO& io, cudaStream_t st);
+
 // Message for ewh_last_error(NULL) of calls that have no context.
 void set_global_error(const std::string& msg);
 

@@ -18,6 +18,7 @@
 //            M^{-1} K u = (1/(rho h^2)) sum_a [ -D_a sigma_{.a} + H_a^{-1} B_a sigma_{.a} ].
 #include <cuda_runtime.h>
 
+#include <cstdio>
 #include <cstdlib>
 
 #include "ewh_internal.cuh"
@@ -757,6 +758,397 @@ cudaError_t launch_minvK(const Geom& g, int order, const T* u, T* out, const T* 
   f.sigma = sigma;
   StepScalars s{};
   return launch_mode<T, 3, false>(g, order, f, s, st, nl);
+}
+
+// ---------------------------------------------------------------------------
+// Order 4 (SBP), 2D, FP32, one right-hand side: every time level of a wave
+// solve in ONE cooperative launch with the state held on chip.
+//
+// One CTA of NT threads per SM owns a wx x wy block of nodes (every block
+// at least 8 x 8, so SBP closure reaches stay inside the halos).  It keeps
+//   in shared memory: u on the block +- 4 nodes, the stresses on the block
+//                     +- 2 nodes, delta on the block;
+//   in registers:     the filter accumulator of its nodes (node t + NT k of
+//                     the block for thread t, k < NK).
+// Per time level a CTA reloads only the 4-node halo ring of u (its
+// neighbours' rims, written at the previous level to a global exchange
+// buffer), recomputes the stresses on block +- 2 from u on block +- 4, forms
+// -D sigma + H^{-1} B sigma and the leapfrog/filter update of its own nodes
+// (same arithmetic as the split kernels), writes its own 4-node rim to the
+// other exchange buffer and meets the other CTAs at a grid barrier: one
+// barrier per level; lambda, mu, 1/(rho h^2) (and f/rho) are the only other
+// global reads.  Barrier waits are bounded in time; on a timeout the kernel raises
+// an error flag, every CTA leaves at its next barrier and fills its
+// accumulator nodes with NaN, which the solve reports as a breakdown.
+// ---------------------------------------------------------------------------
+constexpr int RS_HU = 4;  // u halo
+constexpr int RS_HS = 2;  // stress halo
+constexpr unsigned long long RS_TIMEOUT_NS = 1000000000ull;  // one barrier wait, 1 s
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier: returns false if it (or another CTA) gave up.
+__device__ __forceinline__ bool rs_grid_barrier(unsigned* bar, unsigned target, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (ld_acquire_gpu(bar + 1) != 0u) {
+      ok = 0;
+    } else {
+      __threadfence();  // the CTA's writes (ordered by the barrier above) before the arrival
+      atomicAdd(bar, 1u);
+      const unsigned long long t0 = global_ns();
+      unsigned spins = 0;
+      while (ld_acquire_gpu(bar) < target) {
+        if (ld_acquire_gpu(bar + 1) != 0u) {
+          ok = 0;
+          break;
+        }
+        if (++spins > (1u << 26) || global_ns() - t0 > RS_TIMEOUT_NS) {
+          atomicExch(bar + 1, 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+      __threadfence();
+    }
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+__device__ __forceinline__ bool rs_closure(int x, int n) { return x < 4 || x > n - 5; }
+
+struct ResidentShape {
+  int px, bx, by;
+};
+
+template <int NT, int NK>
+__global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShape sh, ResidentIO io) {
+  if (g.dim != 2) return;
+  extern __shared__ float rs_smem[];
+  __shared__ int s_ok;
+  const int n0 = g.n[0], n1 = g.n[1];
+  const int X0 = (blockIdx.x % sh.px) * sh.bx, Y0 = (blockIdx.x / sh.px) * sh.by;
+  const int wx = min(sh.bx, n0 - X0), wy = min(sh.by, n1 - Y0);
+  const int UX = sh.bx + 2 * RS_HU, UY = sh.by + 2 * RS_HU;  // u tile row stride / rows
+  const int SX = sh.bx + 2 * RS_HS, SY = sh.by + 2 * RS_HS;  // stress tile
+  float* su = rs_smem;              // [2][UY][UX]
+  float* ss = su + 2 * UX * UY;     // [3][SY][SX]: xx, yy, xy
+  float* sdl = ss + 3 * SX * SY;    // [2][by][bx]: delta of the own nodes
+  const int UF = UX * UY, SF = SX * SY;
+  const int t = threadIdx.x;
+  const int F = (int)g.field;  // < 2^31 (checked at creation)
+  const int npx = g.np[0];
+  // padded offset of block node (ix, iy) (ix, iy may lie in the halo)
+  const int obase = (Y0 + PAD) * npx + X0 + PAD;
+  const int ux = wx + 2 * RS_HU, uy = wy + 2 * RS_HU;
+  const int sxn = wx + 2 * RS_HS, syn = wy + 2 * RS_HS;
+  const int nown = wx * wy;
+
+  for (int i = t; i < ux * uy; i += NT) {
+    const int lx = i % ux, ly = i / ux;
+    const int o = obase + (ly - RS_HU) * npx + (lx - RS_HU);
+    su[ly * UX + lx] = __ldcg(io.u0 + o);
+    su[UF + ly * UX + lx] = __ldcg(io.u0 + F + o);
+  }
+  // walk of this thread's own nodes: l = t + 1024 k -> (ix, iy)
+  const int ix0 = t % wx, iy0 = t / wx;
+  const int qstep = NT / wx, rstep = NT % wx;
+  const int DF = sh.bx * sh.by;
+  float ac0[NK], ac1[NK];
+#pragma unroll
+  for (int k = 0; k < NK; ++k) ac0[k] = ac1[k] = 0.f;
+  const float kt = (float)io.kt, w0 = (float)io.w0;
+  const float inv_h0 = 48.0f / 17.0f;
+  bool alive = true;
+  __syncthreads();
+
+  for (int n = 0; n < io.nsteps; ++n) {
+    if (n > 0) {  // halo ring of u^n from the neighbours' rims
+      const float* xb = (n & 1) ? io.xbuf1 : io.xbuf0;
+      for (int i = t; i < ux * uy; i += NT) {
+        const int lx = i % ux, ly = i / ux;
+        const int ix = lx - RS_HU, iy = ly - RS_HU;
+        if (ix >= 0 && ix < wx && iy >= 0 && iy < wy) continue;
+        const int o = obase + iy * npx + ix;
+        su[ly * UX + lx] = __ldcg(xb + o);
+        su[UF + ly * UX + lx] = __ldcg(xb + F + o);
+      }
+      __syncthreads();
+    }
+    // stresses on the block +- 2 (inside the grid)
+    for (int i = t; i < sxn * syn; i += NT) {
+      const int qx = i % sxn, qy = i / sxn;
+      const int x = X0 + qx - RS_HS, y = Y0 + qy - RS_HS;
+      if (x < 0 || x >= n0 || y < 0 || y >= n1) continue;
+      const int o = obase + (qy - RS_HS) * npx + (qx - RS_HS);
+      const float l = __ldg(io.lam + o), m = __ldg(io.mu + o);
+      const float* U = su + (qy + RS_HU - RS_HS) * UX + (qx + RS_HU - RS_HS);
+      const float* V = U + UF;
+      float u_x, v_x, u_y, v_y;
+      if (rs_closure(x, n0)) {
+        u_x = sbp_d1<float>(U, 1, x, n0);
+        v_x = sbp_d1<float>(V, 1, x, n0);
+      } else {
+        u_x = c4(U[-2], U[-1], U[1], U[2]);
+        v_x = c4(V[-2], V[-1], V[1], V[2]);
+      }
+      if (rs_closure(y, n1)) {
+        u_y = sbp_d1<float>(U, UX, y, n1);
+        v_y = sbp_d1<float>(V, UX, y, n1);
+      } else {
+        u_y = c4(U[-2 * UX], U[-UX], U[UX], U[2 * UX]);
+        v_y = c4(V[-2 * UX], V[-UX], V[UX], V[2 * UX]);
+      }
+      const float div = u_x + v_y;
+      float* S = ss + qy * SX + qx;
+      S[0] = l * div + 2.0f * m * u_x;
+      S[SF] = l * div + 2.0f * m * v_y;
+      S[2 * SF] = m * (u_y + v_x);
+    }
+    __syncthreads();
+    // divergence and leapfrog/filter update of the own nodes
+    const bool last = n == io.nsteps - 1;
+    const float cosn = (float)io.cosn[n], wnew = (float)io.wnew[n];
+    float* xo = (n & 1) ? io.xbuf0 : io.xbuf1;  // rims of u^{n+1}
+    int ix = ix0, iy = iy0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+      if (t + k * NT < nown) {
+        const int x = X0 + ix, y = Y0 + iy;
+        float* Uo = su + (iy + RS_HU) * UX + (ix + RS_HU);
+        if (is_unknown(g, x, y, 0)) {
+          const float* Sxx = ss + (iy + RS_HS) * SX + (ix + RS_HS);
+          const float* Syy = Sxx + SF;
+          const float* Sxy = Sxx + 2 * SF;
+          float kxu, kxv, kyu, kyv;
+          if (rs_closure(x, n0)) {
+            kxu = sbp_d1<float>(Sxx, 1, x, n0);
+            kxv = sbp_d1<float>(Sxy, 1, x, n0);
+          } else {
+            kxu = c4(Sxx[-2], Sxx[-1], Sxx[1], Sxx[2]);
+            kxv = c4(Sxy[-2], Sxy[-1], Sxy[1], Sxy[2]);
+          }
+          if (rs_closure(y, n1)) {
+            kyu = sbp_d1<float>(Sxy, SX, y, n1);
+            kyv = sbp_d1<float>(Syy, SX, y, n1);
+          } else {
+            kyu = c4(Sxy[-2 * SX], Sxy[-SX], Sxy[SX], Sxy[2 * SX]);
+            kyv = c4(Syy[-2 * SX], Syy[-SX], Syy[SX], Syy[2 * SX]);
+          }
+          float ku = -kxu - kyu;
+          float kv = -kxv - kyv;
+          if (x == 0) {
+            ku -= inv_h0 * Sxx[0];
+            kv -= inv_h0 * Sxy[0];
+          } else if (x == n0 - 1) {
+            ku += inv_h0 * Sxx[0];
+            kv += inv_h0 * Sxy[0];
+          }
+          if (y == 0) {
+            ku -= inv_h0 * Sxy[0];
+            kv -= inv_h0 * Syy[0];
+          } else if (y == n1 - 1) {
+            ku += inv_h0 * Sxy[0];
+            kv += inv_h0 * Syy[0];
+          }
+          const int o = obase + iy * npx + ix;
+          const float irh = __ldg(io.irh2 + o);
+          float au = ku * irh, av = kv * irh;
+          if (io.frho) {
+            au += __ldg(io.frho + o) * cosn;
+            av += __ldg(io.frho + F + o) * cosn;
+          }
+          const float uu = Uo[0], uv = Uo[UF];
+          float* D = sdl + iy * sh.bx + ix;
+          float du, dv;
+          if (n == 0) {
+            du = -0.5f * kt * au;
+            dv = -0.5f * kt * av;
+          } else {
+            du = D[0] - kt * au;
+            dv = D[DF] - kt * av;
+          }
+          const float nu_ = uu + du, nv_ = uv + dv;
+          if (n == 0) {
+            ac0[k] = w0 * uu + wnew * nu_;
+            ac1[k] = w0 * uv + wnew * nv_;
+          } else {
+            ac0[k] += wnew * nu_;
+            ac1[k] += wnew * nv_;
+          }
+          D[0] = du;
+          D[DF] = dv;
+          if (!last) {
+            Uo[0] = nu_;
+            Uo[UF] = nv_;
+          }
+        }
+        if (!last && (ix < RS_HU || ix >= wx - RS_HU || iy < RS_HU || iy >= wy - RS_HU)) {
+          const int o = obase + iy * npx + ix;
+          xo[o] = Uo[0];
+          xo[F + o] = Uo[UF];
+        }
+      }
+      ix += rstep;
+      iy += qstep;
+      if (ix >= wx) {
+        ix -= wx;
+        ++iy;
+      }
+    }
+    if (!last && !rs_grid_barrier(io.bar, (unsigned)(n + 1) * gridDim.x, &s_ok)) {
+      alive = false;
+      break;
+    }
+  }
+  // accumulator of the own unknowns (NaN when the barrier gave up)
+  const float nanv = __int_as_float(0x7fc00000);
+  int ix = ix0, iy = iy0;
+#pragma unroll
+  for (int k = 0; k < NK; ++k) {
+    if (t + k * NT < nown) {
+      const int x = X0 + ix, y = Y0 + iy;
+      if (is_unknown(g, x, y, 0)) {
+        const int o = obase + iy * npx + ix;
+        io.acc[o] = alive ? ac0[k] : nanv;
+        io.acc[F + o] = alive ? ac1[k] : nanv;
+      }
+    }
+    ix += rstep;
+    iy += qstep;
+    if (ix >= wx) {
+      ix -= wx;
+      ++iy;
+    }
+  }
+}
+
+static size_t resident_smem(int bx, int by) {
+  return sizeof(float) * ((size_t)2 * (bx + 2 * RS_HU) * (by + 2 * RS_HU) + (size_t)3 * (bx + 2 * RS_HS) * (by + 2 * RS_HS) +
+                          (size_t)2 * bx * by);
+}
+
+// Opt the kernel in to the device's largest dynamic shared memory (the same
+// value for every context, so plans of different sizes never undo each
+// other; set before any launch or capture) and report CTAs per SM at smem.
+template <int NT, int NK>
+static cudaError_t resident_prepare(int smem_max, size_t smem, int* per_sm) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, step2d_o4_resident<NT, NK>);
+  if (e != cudaSuccess) return e;
+  const int dyn_max = smem_max - (int)fa.sharedSizeBytes;  // static + dynamic <= opt-in limit
+  if ((long long)smem > dyn_max) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(step2d_o4_resident<NT, NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step2d_o4_resident<NT, NK>, NT, smem);
+}
+
+static cudaError_t resident_prepare_shape(int shape, int smem_max, size_t smem, int* per_sm) {
+  switch (shape) {
+    case 0: return resident_prepare<RS_SHAPE_THREADS[0], RS_SHAPE_NODES[0]>(smem_max, smem, per_sm);
+    case 1: return resident_prepare<RS_SHAPE_THREADS[1], RS_SHAPE_NODES[1]>(smem_max, smem, per_sm);
+    case 2: return resident_prepare<RS_SHAPE_THREADS[2], RS_SHAPE_NODES[2]>(smem_max, smem, per_sm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+ResidentPlan plan_resident_o4(const Geom& g, int shape) {
+  ResidentPlan best;
+  if (g.dim != 2 || g.nrhs != 1 || g.field >= (1LL << 31) || shape < 0 || shape >= RS_SHAPES) return best;
+  int dev = 0, sms = 0, smem_max = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) {
+    cudaGetLastError();
+    return best;
+  }
+  const long long cap = (long long)RS_SHAPE_THREADS[shape] * RS_SHAPE_NODES[shape];
+  const int n0 = g.n[0], n1 = g.n[1];
+  long long best_cost = -1;
+  for (int px = 1; px <= sms && px <= n0 / 8; ++px) {
+    const int bx = (n0 + px - 1) / px;
+    const int pxa = (n0 + bx - 1) / bx;
+    if (n0 - (pxa - 1) * bx < 8) continue;
+    for (int py = 1; pxa * py <= sms && py <= n1 / 8; ++py) {
+      const int by = (n1 + py - 1) / py;
+      const int pya = (n1 + by - 1) / by;
+      if (n1 - (pya - 1) * by < 8) continue;
+      if ((long long)bx * by > cap) continue;
+      const size_t sm = resident_smem(bx, by);
+      if (sm > (size_t)smem_max) continue;
+      // per-CTA work: u tile + stress tile (the CTAs run in lockstep)
+      const long long cost =
+          (long long)(bx + 2 * RS_HU) * (by + 2 * RS_HU) + (long long)(bx + 2 * RS_HS) * (by + 2 * RS_HS);
+      if (best_cost < 0 || cost < best_cost) {
+        best_cost = cost;
+        best.ok = 1;
+        best.shape = shape;
+        best.px = pxa;
+        best.py = pya;
+        best.bx = bx;
+        best.by = by;
+        best.smem = sm;
+      }
+    }
+  }
+  if (!best.ok) return best;
+  // every CTA must be resident at once
+  int per_sm = 0;
+  const cudaError_t e = resident_prepare_shape(shape, smem_max, best.smem, &per_sm);
+  const bool verbose = getenv("EWH_VERBOSE") != nullptr;
+  if (e != cudaSuccess || (long long)per_sm * sms < (long long)best.px * best.py) {
+    if (verbose)
+      fprintf(stderr, "ewh: resident shape %d unusable (%s, %d CTA/SM, %d x %d CTAs)\n", shape, cudaGetErrorString(e),
+              per_sm, best.px, best.py);
+    cudaGetLastError();
+    return ResidentPlan{};
+  }
+  if (verbose)
+    fprintf(stderr, "ewh: resident shape %d: %d x %d CTAs of %d x %d nodes, %zu B shared\n", shape, best.px, best.py,
+            best.bx, best.by, best.smem);
+  return best;
+}
+
+template <int NT, int NK>
+static cudaError_t resident_launch(const Geom& g, const ResidentPlan& p, const ResidentIO& io, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(p.px * p.py);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = p.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ResidentShape sh{p.px, p.bx, p.by};
+  return cudaLaunchKernelEx(&cfg, step2d_o4_resident<NT, NK>, g, sh, io);
+}
+
+cudaError_t launch_resident_o4(const Geom& g, const ResidentPlan& p, const ResidentIO& io, cudaStream_t st) {
+  if (!p.ok || g.dim != 2 || g.nrhs != 1 || io.nsteps < 1) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(io.bar, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  switch (p.shape) {
+    case 0: return resident_launch<RS_SHAPE_THREADS[0], RS_SHAPE_NODES[0]>(g, p, io, st);
+    case 1: return resident_launch<RS_SHAPE_THREADS[1], RS_SHAPE_NODES[1]>(g, p, io, st);
+    case 2: return resident_launch<RS_SHAPE_THREADS[2], RS_SHAPE_NODES[2]>(g, p, io, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template cudaError_t launch_step<float>(const Geom&, int, const WaveFields<float>&, StepMode,

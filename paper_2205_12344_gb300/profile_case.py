@@ -1,0 +1,43 @@
+"""A small, self-contained run of the step kernels for profilers (ncu).
+
+Applies S (one period of the corrected leapfrog with the trapezoid filter,
+eqs. (qoper) and (elastic-time-explicit-corrected)) a few times to a random
+vector on the layered 2D medium of the benchmark (order-4 SBP operator,
+1024^2 nodes by default), then exits.  Every launch it makes is one of the
+library's own kernels; the state is ~60 MB per right-hand side in FP32, so a
+capture of one or two launches stays small.
+
+    python -m paper_2205_12344_gb300.profile_case --nu 1024 --nrhs 1 --precision fp32 --applies 2
+"""
+from __future__ import annotations
+
+import argparse
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--nu", type=int, default=1024, help="nodes per axis")
+    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides (shots) per launch")
+    ap.add_argument("--precision", default="fp32", choices=("fp32", "fp64"))
+    ap.add_argument("--applies", type=int, default=2, help="applications of S")
+    a = ap.parse_args(argv)
+
+    import torch
+
+    from . import inputs
+    from .api import WaveHoltz
+
+    p = inputs.cfg_layered_2d(nu=a.nu, order=4, nrhs=a.nrhs, shot_x=[2.0 + 1.5 * k for k in range(a.nrhs)])
+    with WaveHoltz(p, precision=a.precision) as wh:
+        g = torch.Generator(device="cuda").manual_seed(7)
+        v = torch.randn(wh.n, dtype=torch.float64, device="cuda", generator=g)
+        o = None
+        for _ in range(a.applies):
+            o = wh.apply_S(v)
+        torch.cuda.synchronize()
+        info = wh.stats()
+        print("applies %d  |S v| %.6e  launches %d" % (a.applies, float(o.norm()), int(info.launches)))
+
+
+if __name__ == "__main__":
+    main()
