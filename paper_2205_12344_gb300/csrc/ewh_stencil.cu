@@ -834,6 +834,34 @@ struct ResidentShape {
   int px, bx, by;
 };
 
+// The shared-memory layout is fixed at compile time (so every stencil and
+// plane offset is an immediate): blocks are at most RS_BXMAX x RS_BYMAX nodes.
+constexpr int RS_BXMAX = 132;
+constexpr int RS_BYMAX = 54;
+constexpr int RS_UX = RS_BXMAX + 2 * RS_HU;  // u tile row stride
+constexpr int RS_SX = RS_BXMAX + 2 * RS_HS;  // stress tile row stride
+constexpr int RS_UPLANE = (RS_BYMAX + 2 * RS_HU) * RS_UX;
+constexpr int RS_SPLANE = (RS_BYMAX + 2 * RS_HS) * RS_SX;
+constexpr int RS_DPLANE = RS_BYMAX * RS_BXMAX;
+constexpr int RS_OFF_V = RS_UPLANE;              // u, component 1
+constexpr int RS_OFF_XX = 2 * RS_UPLANE;         // stresses xx, yy, xy
+constexpr int RS_OFF_YY = RS_OFF_XX + RS_SPLANE;
+constexpr int RS_OFF_XY = RS_OFF_YY + RS_SPLANE;
+constexpr int RS_OFF_DU = RS_OFF_XY + RS_SPLANE;  // delta, components 0 and 1
+constexpr int RS_OFF_DV = RS_OFF_DU + RS_DPLANE;
+constexpr int RS_FLOATS = RS_OFF_DV + RS_DPLANE;
+
+// Advance a thread's position in a w-wide row-major walk by (sx, sy) = the
+// thread count split into whole rows and a remainder.
+__device__ __forceinline__ void walk_next(int& x, int& y, int w, int sx, int sy) {
+  x += sx;
+  y += sy;
+  if (x >= w) {
+    x -= w;
+    ++y;
+  }
+}
+
 template <int NT, int NK>
 __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShape sh, ResidentIO io) {
   if (g.dim != 2) return;
@@ -842,31 +870,38 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
   const int n0 = g.n[0], n1 = g.n[1];
   const int X0 = (blockIdx.x % sh.px) * sh.bx, Y0 = (blockIdx.x / sh.px) * sh.by;
   const int wx = min(sh.bx, n0 - X0), wy = min(sh.by, n1 - Y0);
-  const int UX = sh.bx + 2 * RS_HU, UY = sh.by + 2 * RS_HU;  // u tile row stride / rows
-  const int SX = sh.bx + 2 * RS_HS, SY = sh.by + 2 * RS_HS;  // stress tile
-  float* su = rs_smem;              // [2][UY][UX]
-  float* ss = su + 2 * UX * UY;     // [3][SY][SX]: xx, yy, xy
-  float* sdl = ss + 3 * SX * SY;    // [2][by][bx]: delta of the own nodes
-  const int UF = UX * UY, SF = SX * SY;
+  // u: [RS_BYMAX + 8][RS_UX] per component, block node (0, 0) at (4, 4);
+  // stresses: [RS_BYMAX + 4][RS_SX], block node (0, 0) at (2, 2);
+  // delta of the own nodes: [RS_BYMAX][RS_BXMAX]
+  float* const su = rs_smem;
+  float* const sv = rs_smem + RS_OFF_V;
+  float* const sxx = rs_smem + RS_OFF_XX;
+  float* const syy = rs_smem + RS_OFF_YY;
+  float* const sxy = rs_smem + RS_OFF_XY;
+  float* const sdu = rs_smem + RS_OFF_DU;
+  float* const sdv = rs_smem + RS_OFF_DV;
   const int t = threadIdx.x;
   const int F = (int)g.field;  // < 2^31 (checked at creation)
   const int npx = g.np[0];
-  // padded offset of block node (ix, iy) (ix, iy may lie in the halo)
-  const int obase = (Y0 + PAD) * npx + X0 + PAD;
+  const int obase = (Y0 + PAD) * npx + X0 + PAD;        // padded offset of block node (0, 0)
+  const int ubase = obase - RS_HU * npx - RS_HU;         // ... of u tile position (0, 0)
   const int ux = wx + 2 * RS_HU, uy = wy + 2 * RS_HU;
   const int sxn = wx + 2 * RS_HS, syn = wy + 2 * RS_HS;
   const int nown = wx * wy;
+  const bool lf0 = g.lo_free[0], hf0 = g.hi_free[0], lf1 = g.lo_free[1], hf1 = g.hi_free[1];
 
-  for (int i = t; i < ux * uy; i += NT) {
-    const int lx = i % ux, ly = i / ux;
-    const int o = obase + (ly - RS_HU) * npx + (lx - RS_HU);
-    su[ly * UX + lx] = __ldcg(io.u0 + o);
-    su[UF + ly * UX + lx] = __ldcg(io.u0 + F + o);
+  {  // u^0 on the whole tile
+    int lx = t % ux, ly = t / ux;
+    const int rx = NT % ux, ry = NT / ux;
+    for (; ly < uy; walk_next(lx, ly, ux, rx, ry)) {
+      const int o = ubase + ly * npx + lx;
+      su[ly * RS_UX + lx] = __ldcg(io.u0 + o);
+      sv[ly * RS_UX + lx] = __ldcg(io.u0 + F + o);
+    }
   }
-  // walk of this thread's own nodes: l = t + 1024 k -> (ix, iy)
+  // walk of this thread's own nodes: l = t + NT k -> (ix, iy)
   const int ix0 = t % wx, iy0 = t / wx;
   const int qstep = NT / wx, rstep = NT % wx;
-  const int DF = sh.bx * sh.by;
   float ac0[NK], ac1[NK];
 #pragma unroll
   for (int k = 0; k < NK; ++k) ac0[k] = ac1[k] = 0.f;
@@ -878,45 +913,57 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
   for (int n = 0; n < io.nsteps; ++n) {
     if (n > 0) {  // halo ring of u^n from the neighbours' rims
       const float* xb = (n & 1) ? io.xbuf1 : io.xbuf0;
-      for (int i = t; i < ux * uy; i += NT) {
-        const int lx = i % ux, ly = i / ux;
-        const int ix = lx - RS_HU, iy = ly - RS_HU;
-        if (ix >= 0 && ix < wx && iy >= 0 && iy < wy) continue;
-        const int o = obase + iy * npx + ix;
-        su[ly * UX + lx] = __ldcg(xb + o);
-        su[UF + ly * UX + lx] = __ldcg(xb + F + o);
+      {  // top and bottom strips: tile rows 0..3 and wy+4..wy+7, all columns
+        int lx = t % ux, r = t / ux;
+        const int rx = NT % ux, ry = NT / ux;
+        for (; r < 2 * RS_HU; walk_next(lx, r, ux, rx, ry)) {
+          const int ly = r < RS_HU ? r : wy + r;
+          const int o = ubase + ly * npx + lx;
+          su[ly * RS_UX + lx] = __ldcg(xb + o);
+          sv[ly * RS_UX + lx] = __ldcg(xb + F + o);
+        }
+      }
+      for (int i = t; i < 2 * RS_HU * wy; i += NT) {  // side strips: columns 0..3 and wx+4..wx+7
+        const int c = i & (2 * RS_HU - 1), ly = RS_HU + (i >> 3);
+        const int lx = c < RS_HU ? c : wx + c;
+        const int o = ubase + ly * npx + lx;
+        su[ly * RS_UX + lx] = __ldcg(xb + o);
+        sv[ly * RS_UX + lx] = __ldcg(xb + F + o);
       }
       __syncthreads();
     }
-    // stresses on the block +- 2 (inside the grid)
-    for (int i = t; i < sxn * syn; i += NT) {
-      const int qx = i % sxn, qy = i / sxn;
-      const int x = X0 + qx - RS_HS, y = Y0 + qy - RS_HS;
-      if (x < 0 || x >= n0 || y < 0 || y >= n1) continue;
-      const int o = obase + (qy - RS_HS) * npx + (qx - RS_HS);
-      const float l = __ldg(io.lam + o), m = __ldg(io.mu + o);
-      const float* U = su + (qy + RS_HU - RS_HS) * UX + (qx + RS_HU - RS_HS);
-      const float* V = U + UF;
-      float u_x, v_x, u_y, v_y;
-      if (rs_closure(x, n0)) {
-        u_x = sbp_d1<float>(U, 1, x, n0);
-        v_x = sbp_d1<float>(V, 1, x, n0);
-      } else {
-        u_x = c4(U[-2], U[-1], U[1], U[2]);
-        v_x = c4(V[-2], V[-1], V[1], V[2]);
+    {  // stresses on the block +- 2 (inside the grid)
+      int qx = t % sxn, qy = t / sxn;
+      const int rx = NT % sxn, ry = NT / sxn;
+      for (; qy < syn; walk_next(qx, qy, sxn, rx, ry)) {
+        const int x = X0 + qx - RS_HS, y = Y0 + qy - RS_HS;
+        if (x < 0 || x >= n0 || y < 0 || y >= n1) continue;
+        const int o = obase + (qy - RS_HS) * npx + (qx - RS_HS);
+        const float l = __ldg(io.lam + o), m = __ldg(io.mu + o);
+        const int pu = (qy + RS_HU - RS_HS) * RS_UX + (qx + RS_HU - RS_HS);
+        const float* U = su + pu;
+        const float* V = sv + pu;
+        float u_x, v_x, u_y, v_y;
+        if (x < 4 || x > n0 - 5) {
+          u_x = sbp_d1<float>(U, 1, x, n0);
+          v_x = sbp_d1<float>(V, 1, x, n0);
+        } else {
+          u_x = c4(U[-2], U[-1], U[1], U[2]);
+          v_x = c4(V[-2], V[-1], V[1], V[2]);
+        }
+        if (y < 4 || y > n1 - 5) {
+          u_y = sbp_d1<float>(U, RS_UX, y, n1);
+          v_y = sbp_d1<float>(V, RS_UX, y, n1);
+        } else {
+          u_y = c4(U[-2 * RS_UX], U[-RS_UX], U[RS_UX], U[2 * RS_UX]);
+          v_y = c4(V[-2 * RS_UX], V[-RS_UX], V[RS_UX], V[2 * RS_UX]);
+        }
+        const float div = u_x + v_y;
+        const int ps = qy * RS_SX + qx;
+        sxx[ps] = l * div + 2.0f * m * u_x;
+        syy[ps] = l * div + 2.0f * m * v_y;
+        sxy[ps] = m * (u_y + v_x);
       }
-      if (rs_closure(y, n1)) {
-        u_y = sbp_d1<float>(U, UX, y, n1);
-        v_y = sbp_d1<float>(V, UX, y, n1);
-      } else {
-        u_y = c4(U[-2 * UX], U[-UX], U[UX], U[2 * UX]);
-        v_y = c4(V[-2 * UX], V[-UX], V[UX], V[2 * UX]);
-      }
-      const float div = u_x + v_y;
-      float* S = ss + qy * SX + qx;
-      S[0] = l * div + 2.0f * m * u_x;
-      S[SF] = l * div + 2.0f * m * v_y;
-      S[2 * SF] = m * (u_y + v_x);
     }
     __syncthreads();
     // divergence and leapfrog/filter update of the own nodes
@@ -928,25 +975,27 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
     for (int k = 0; k < NK; ++k) {
       if (t + k * NT < nown) {
         const int x = X0 + ix, y = Y0 + iy;
-        float* Uo = su + (iy + RS_HU) * UX + (ix + RS_HU);
-        if (is_unknown(g, x, y, 0)) {
-          const float* Sxx = ss + (iy + RS_HS) * SX + (ix + RS_HS);
-          const float* Syy = Sxx + SF;
-          const float* Sxy = Sxx + 2 * SF;
+        const int pu = (iy + RS_HU) * RS_UX + (ix + RS_HU);
+        const bool unk = (x > 0 || lf0) && (x < n0 - 1 || hf0) && (y > 0 || lf1) && (y < n1 - 1 || hf1);
+        if (unk) {
+          const int ps = (iy + RS_HS) * RS_SX + (ix + RS_HS);
+          const float* Sxx = sxx + ps;
+          const float* Syy = syy + ps;
+          const float* Sxy = sxy + ps;
           float kxu, kxv, kyu, kyv;
-          if (rs_closure(x, n0)) {
+          if (x < 4 || x > n0 - 5) {
             kxu = sbp_d1<float>(Sxx, 1, x, n0);
             kxv = sbp_d1<float>(Sxy, 1, x, n0);
           } else {
             kxu = c4(Sxx[-2], Sxx[-1], Sxx[1], Sxx[2]);
             kxv = c4(Sxy[-2], Sxy[-1], Sxy[1], Sxy[2]);
           }
-          if (rs_closure(y, n1)) {
-            kyu = sbp_d1<float>(Sxy, SX, y, n1);
-            kyv = sbp_d1<float>(Syy, SX, y, n1);
+          if (y < 4 || y > n1 - 5) {
+            kyu = sbp_d1<float>(Sxy, RS_SX, y, n1);
+            kyv = sbp_d1<float>(Syy, RS_SX, y, n1);
           } else {
-            kyu = c4(Sxy[-2 * SX], Sxy[-SX], Sxy[SX], Sxy[2 * SX]);
-            kyv = c4(Syy[-2 * SX], Syy[-SX], Syy[SX], Syy[2 * SX]);
+            kyu = c4(Sxy[-2 * RS_SX], Sxy[-RS_SX], Sxy[RS_SX], Sxy[2 * RS_SX]);
+            kyv = c4(Syy[-2 * RS_SX], Syy[-RS_SX], Syy[RS_SX], Syy[2 * RS_SX]);
           }
           float ku = -kxu - kyu;
           float kv = -kxv - kyv;
@@ -971,15 +1020,15 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
             au += __ldg(io.frho + o) * cosn;
             av += __ldg(io.frho + F + o) * cosn;
           }
-          const float uu = Uo[0], uv = Uo[UF];
-          float* D = sdl + iy * sh.bx + ix;
+          const int pd = iy * RS_BXMAX + ix;
+          const float uu = su[pu], uv = sv[pu];
           float du, dv;
           if (n == 0) {
             du = -0.5f * kt * au;
             dv = -0.5f * kt * av;
           } else {
-            du = D[0] - kt * au;
-            dv = D[DF] - kt * av;
+            du = sdu[pd] - kt * au;
+            dv = sdv[pd] - kt * av;
           }
           const float nu_ = uu + du, nv_ = uv + dv;
           if (n == 0) {
@@ -989,25 +1038,20 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
             ac0[k] += wnew * nu_;
             ac1[k] += wnew * nv_;
           }
-          D[0] = du;
-          D[DF] = dv;
+          sdu[pd] = du;
+          sdv[pd] = dv;
           if (!last) {
-            Uo[0] = nu_;
-            Uo[UF] = nv_;
+            su[pu] = nu_;
+            sv[pu] = nv_;
           }
         }
         if (!last && (ix < RS_HU || ix >= wx - RS_HU || iy < RS_HU || iy >= wy - RS_HU)) {
           const int o = obase + iy * npx + ix;
-          xo[o] = Uo[0];
-          xo[F + o] = Uo[UF];
+          xo[o] = su[pu];
+          xo[F + o] = sv[pu];
         }
       }
-      ix += rstep;
-      iy += qstep;
-      if (ix >= wx) {
-        ix -= wx;
-        ++iy;
-      }
+      walk_next(ix, iy, wx, rstep, qstep);
     }
     if (!last && !rs_grid_barrier(io.bar, (unsigned)(n + 1) * gridDim.x, &s_ok)) {
       alive = false;
@@ -1021,25 +1065,17 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
   for (int k = 0; k < NK; ++k) {
     if (t + k * NT < nown) {
       const int x = X0 + ix, y = Y0 + iy;
-      if (is_unknown(g, x, y, 0)) {
+      if ((x > 0 || lf0) && (x < n0 - 1 || hf0) && (y > 0 || lf1) && (y < n1 - 1 || hf1)) {
         const int o = obase + iy * npx + ix;
         io.acc[o] = alive ? ac0[k] : nanv;
         io.acc[F + o] = alive ? ac1[k] : nanv;
       }
     }
-    ix += rstep;
-    iy += qstep;
-    if (ix >= wx) {
-      ix -= wx;
-      ++iy;
-    }
+    walk_next(ix, iy, wx, rstep, qstep);
   }
 }
 
-static size_t resident_smem(int bx, int by) {
-  return sizeof(float) * ((size_t)2 * (bx + 2 * RS_HU) * (by + 2 * RS_HU) + (size_t)3 * (bx + 2 * RS_HS) * (by + 2 * RS_HS) +
-                          (size_t)2 * bx * by);
-}
+static size_t resident_smem() { return sizeof(float) * (size_t)RS_FLOATS; }
 
 // Opt the kernel in to the device's largest dynamic shared memory (the same
 // value for every context, so plans of different sizes never undo each
@@ -1087,8 +1123,8 @@ ResidentPlan plan_resident_o4(const Geom& g, int shape) {
       const int by = (n1 + py - 1) / py;
       const int pya = (n1 + by - 1) / by;
       if (n1 - (pya - 1) * by < 8) continue;
-      if ((long long)bx * by > cap) continue;
-      const size_t sm = resident_smem(bx, by);
+      if ((long long)bx * by > cap || bx > RS_BXMAX || by > RS_BYMAX) continue;
+      const size_t sm = resident_smem();
       if (sm > (size_t)smem_max) continue;
       // per-CTA work: u tile + stress tile (the CTAs run in lockstep)
       const long long cost =
