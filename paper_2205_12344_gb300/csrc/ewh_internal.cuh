@@ -145,6 +145,8 @@ struct ResidentPlan {
   int shape = 0;       // index into RS_SHAPE_*
   int px = 0, py = 0;  // CTAs per axis
   int bx = 0, by = 0;  // node block per CTA (the last block per axis may be smaller, >= 8)
+  int ex = 0;          // width of the first block along x (the x-closure columns cost more, so the
+                       // first and last blocks along x are narrower); the last is the remainder
   size_t smem = 0;     // dynamic shared memory per CTA in bytes
 };
 // Partition of g for the current device and a CTA shape (ok = 0 when g does

@@ -18,6 +18,8 @@
 //            M^{-1} K u = (1/(rho h^2)) sum_a [ -D_a sigma_{.a} + H_a^{-1} B_a sigma_{.a} ].
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 
@@ -796,7 +798,14 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Grid barrier: returns false if it (or another CTA) gave up.
+// Grid barrier: returns false if it (or another CTA) gave up.  After a
+// __syncthreads that orders the CTA's writes, thread 0 counts the CTA in with
+// a release add and polls with acquire loads; the error flag and the time
+// limit are looked at every 256 polls.
+__device__ __forceinline__ void red_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ bool rs_grid_barrier(unsigned* bar, unsigned target, int* s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -804,23 +813,21 @@ __device__ __forceinline__ bool rs_grid_barrier(unsigned* bar, unsigned target, 
     if (ld_acquire_gpu(bar + 1) != 0u) {
       ok = 0;
     } else {
-      __threadfence();  // the CTA's writes (ordered by the barrier above) before the arrival
-      atomicAdd(bar, 1u);
+      red_release_gpu(bar, 1u);
       const unsigned long long t0 = global_ns();
-      unsigned spins = 0;
-      while (ld_acquire_gpu(bar) < target) {
-        if (ld_acquire_gpu(bar + 1) != 0u) {
-          ok = 0;
-          break;
+      for (unsigned spins = 1; ld_acquire_gpu(bar) < target; ++spins) {
+        if ((spins & 255u) == 0u) {
+          if (ld_acquire_gpu(bar + 1) != 0u) {
+            ok = 0;
+            break;
+          }
+          if (spins > (1u << 22) || global_ns() - t0 > RS_TIMEOUT_NS) {
+            atomicExch(bar + 1, 1u);
+            ok = 0;
+            break;
+          }
         }
-        if (++spins > (1u << 26) || global_ns() - t0 > RS_TIMEOUT_NS) {
-          atomicExch(bar + 1, 1u);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
       }
-      __threadfence();
     }
     *s_ok = ok;
   }
@@ -831,7 +838,7 @@ __device__ __forceinline__ bool rs_grid_barrier(unsigned* bar, unsigned target, 
 __device__ __forceinline__ bool rs_closure(int x, int n) { return x < 4 || x > n - 5; }
 
 struct ResidentShape {
-  int px, bx, by;
+  int px, bx, by, ex;  // CTAs along x; interior block width; block height; first block width
 };
 
 // The shared-memory layout is fixed at compile time (so every stencil and
@@ -849,7 +856,28 @@ constexpr int RS_OFF_YY = RS_OFF_XX + RS_SPLANE;
 constexpr int RS_OFF_XY = RS_OFF_YY + RS_SPLANE;
 constexpr int RS_OFF_DU = RS_OFF_XY + RS_SPLANE;  // delta, components 0 and 1
 constexpr int RS_OFF_DV = RS_OFF_DU + RS_DPLANE;
-constexpr int RS_FLOATS = RS_OFF_DV + RS_DPLANE;
+constexpr int RS_OFF_TAB = RS_OFF_DV + RS_DPLANE;  // copy of the SBP closure rows (4 x 6)
+constexpr int RS_FLOATS = RS_OFF_TAB + 24;
+
+// SBP first derivative as sbp_d1, with the closure rows read from the shared
+// copy `tab`: lanes on different closure rows then read different banks
+// instead of serialising on the constant cache.
+__device__ __forceinline__ float rs_sbp_d1(const float* v, int s, int p, int N, const float* tab) {
+  if (p < 4) {
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) acc += tab[p * 6 + j] * v[(j - p) * s];
+    return acc;
+  }
+  if (p > N - 5) {
+    const int r = N - 1 - p;
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) acc -= tab[r * 6 + j] * v[(r - j) * s];
+    return acc;
+  }
+  return (v[-2 * s] - 8.0f * v[-s] + 8.0f * v[s] - v[2 * s]) * (1.0f / 12.0f);
+}
 
 // Advance a thread's position in a w-wide row-major walk by (sx, sy) = the
 // thread count split into whole rows and a remainder.
@@ -868,8 +896,9 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
   extern __shared__ float rs_smem[];
   __shared__ int s_ok;
   const int n0 = g.n[0], n1 = g.n[1];
-  const int X0 = (blockIdx.x % sh.px) * sh.bx, Y0 = (blockIdx.x / sh.px) * sh.by;
-  const int wx = min(sh.bx, n0 - X0), wy = min(sh.by, n1 - Y0);
+  const int cx = blockIdx.x % sh.px;
+  const int X0 = cx == 0 ? 0 : sh.ex + (cx - 1) * sh.bx, Y0 = (blockIdx.x / sh.px) * sh.by;
+  const int wx = cx == 0 ? sh.ex : min(sh.bx, n0 - X0), wy = min(sh.by, n1 - Y0);
   // u: [RS_BYMAX + 8][RS_UX] per component, block node (0, 0) at (4, 4);
   // stresses: [RS_BYMAX + 4][RS_SX], block node (0, 0) at (2, 2);
   // delta of the own nodes: [RS_BYMAX][RS_BXMAX]
@@ -880,6 +909,7 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
   float* const sxy = rs_smem + RS_OFF_XY;
   float* const sdu = rs_smem + RS_OFF_DU;
   float* const sdv = rs_smem + RS_OFF_DV;
+  float* const tab = rs_smem + RS_OFF_TAB;
   const int t = threadIdx.x;
   const int F = (int)g.field;  // < 2^31 (checked at creation)
   const int npx = g.np[0];
@@ -889,6 +919,7 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
   const int sxn = wx + 2 * RS_HS, syn = wy + 2 * RS_HS;
   const int nown = wx * wy;
   const bool lf0 = g.lo_free[0], hf0 = g.hi_free[0], lf1 = g.lo_free[1], hf1 = g.hi_free[1];
+  if (t < 24) tab[t] = c_sbp_f[t / 6][t % 6];
 
   {  // u^0 on the whole tile
     int lx = t % ux, ly = t / ux;
@@ -945,15 +976,15 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
         const float* V = sv + pu;
         float u_x, v_x, u_y, v_y;
         if (x < 4 || x > n0 - 5) {
-          u_x = sbp_d1<float>(U, 1, x, n0);
-          v_x = sbp_d1<float>(V, 1, x, n0);
+          u_x = rs_sbp_d1(U, 1, x, n0, tab);
+          v_x = rs_sbp_d1(V, 1, x, n0, tab);
         } else {
           u_x = c4(U[-2], U[-1], U[1], U[2]);
           v_x = c4(V[-2], V[-1], V[1], V[2]);
         }
         if (y < 4 || y > n1 - 5) {
-          u_y = sbp_d1<float>(U, RS_UX, y, n1);
-          v_y = sbp_d1<float>(V, RS_UX, y, n1);
+          u_y = rs_sbp_d1(U, RS_UX, y, n1, tab);
+          v_y = rs_sbp_d1(V, RS_UX, y, n1, tab);
         } else {
           u_y = c4(U[-2 * RS_UX], U[-RS_UX], U[RS_UX], U[2 * RS_UX]);
           v_y = c4(V[-2 * RS_UX], V[-RS_UX], V[RS_UX], V[2 * RS_UX]);
@@ -984,15 +1015,15 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
           const float* Sxy = sxy + ps;
           float kxu, kxv, kyu, kyv;
           if (x < 4 || x > n0 - 5) {
-            kxu = sbp_d1<float>(Sxx, 1, x, n0);
-            kxv = sbp_d1<float>(Sxy, 1, x, n0);
+            kxu = rs_sbp_d1(Sxx, 1, x, n0, tab);
+            kxv = rs_sbp_d1(Sxy, 1, x, n0, tab);
           } else {
             kxu = c4(Sxx[-2], Sxx[-1], Sxx[1], Sxx[2]);
             kxv = c4(Sxy[-2], Sxy[-1], Sxy[1], Sxy[2]);
           }
           if (y < 4 || y > n1 - 5) {
-            kyu = sbp_d1<float>(Sxy, RS_SX, y, n1);
-            kyv = sbp_d1<float>(Syy, RS_SX, y, n1);
+            kyu = rs_sbp_d1(Sxy, RS_SX, y, n1, tab);
+            kyv = rs_sbp_d1(Syy, RS_SX, y, n1, tab);
           } else {
             kyu = c4(Sxy[-2 * RS_SX], Sxy[-RS_SX], Sxy[RS_SX], Sxy[2 * RS_SX]);
             kyv = c4(Syy[-2 * RS_SX], Syy[-RS_SX], Syy[RS_SX], Syy[2 * RS_SX]);
@@ -1114,28 +1145,42 @@ ResidentPlan plan_resident_o4(const Geom& g, int shape) {
   }
   const long long cap = (long long)RS_SHAPE_THREADS[shape] * RS_SHAPE_NODES[shape];
   const int n0 = g.n[0], n1 = g.n[1];
-  long long best_cost = -1;
+  // Blocks that hold x-closure columns (the first and last along x) take
+  // about RS_EDGE_COST longer per node (a few lanes of their warps diverge):
+  // they get proportionally fewer columns, so all CTAs reach each barrier
+  // together.
+  constexpr double RS_EDGE_COST = 1.1;
+  double best_cost = -1.0;
   for (int px = 1; px <= sms && px <= n0 / 8; ++px) {
-    const int bx = (n0 + px - 1) / px;
-    const int pxa = (n0 + bx - 1) / bx;
-    if (n0 - (pxa - 1) * bx < 8) continue;
-    for (int py = 1; pxa * py <= sms && py <= n1 / 8; ++py) {
+    int bx, ex, last;
+    if (px == 1) {
+      bx = ex = last = n0;
+    } else {
+      bx = px == 2 ? (n0 + 1) / 2 : (int)std::ceil(n0 / (px - 2 + 2.0 / RS_EDGE_COST));
+      ex = px == 2 ? bx : (n0 - (px - 2) * bx) / 2;
+      last = n0 - ex - (px - 2) * bx;
+    }
+    if (ex < 8 || last < 8 || bx > RS_BXMAX || ex > RS_BXMAX || last > RS_BXMAX) continue;
+    const int wmax = std::max(bx, std::max(ex, last));
+    for (int py = 1; px * py <= sms && py <= n1 / 8; ++py) {
       const int by = (n1 + py - 1) / py;
       const int pya = (n1 + by - 1) / by;
       if (n1 - (pya - 1) * by < 8) continue;
-      if ((long long)bx * by > cap || bx > RS_BXMAX || by > RS_BYMAX) continue;
+      if ((long long)wmax * by > cap || by > RS_BYMAX) continue;
       const size_t sm = resident_smem();
       if (sm > (size_t)smem_max) continue;
-      // per-CTA work: u tile + stress tile (the CTAs run in lockstep)
-      const long long cost =
-          (long long)(bx + 2 * RS_HU) * (by + 2 * RS_HU) + (long long)(bx + 2 * RS_HS) * (by + 2 * RS_HS);
+      // per-CTA work (u tile + stress tile) of the slowest block
+      auto work = [&](int w) { return (double)(w + 2 * RS_HU) * (by + 2 * RS_HU) + (double)(w + 2 * RS_HS) * (by + 2 * RS_HS); };
+      const double cost = px == 1 ? work(bx) * RS_EDGE_COST
+                                  : std::max(work(bx), RS_EDGE_COST * work(std::max(ex, last)));
       if (best_cost < 0 || cost < best_cost) {
         best_cost = cost;
         best.ok = 1;
         best.shape = shape;
-        best.px = pxa;
+        best.px = px;
         best.py = pya;
         best.bx = bx;
+        best.ex = ex;
         best.by = by;
         best.smem = sm;
       }
@@ -1154,8 +1199,8 @@ ResidentPlan plan_resident_o4(const Geom& g, int shape) {
     return ResidentPlan{};
   }
   if (verbose)
-    fprintf(stderr, "ewh: resident shape %d: %d x %d CTAs of %d x %d nodes, %zu B shared\n", shape, best.px, best.py,
-            best.bx, best.by, best.smem);
+    fprintf(stderr, "ewh: resident shape %d: %d x %d CTAs of %d (first %d) x %d nodes, %zu B shared\n", shape, best.px,
+            best.py, best.bx, best.ex, best.by, best.smem);
   return best;
 }
 
@@ -1171,7 +1216,7 @@ static cudaError_t resident_launch(const Geom& g, const ResidentPlan& p, const R
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  ResidentShape sh{p.px, p.bx, p.by};
+  ResidentShape sh{p.px, p.bx, p.by, p.ex};
   return cudaLaunchKernelEx(&cfg, step2d_o4_resident<NT, NK>, g, sh, io);
 }
 
