@@ -857,7 +857,40 @@ constexpr int RS_OFF_XY = RS_OFF_YY + RS_SPLANE;
 constexpr int RS_OFF_DU = RS_OFF_XY + RS_SPLANE;  // delta, components 0 and 1
 constexpr int RS_OFF_DV = RS_OFF_DU + RS_DPLANE;
 constexpr int RS_OFF_TAB = RS_OFF_DV + RS_DPLANE;  // copy of the SBP closure rows (4 x 6)
-constexpr int RS_FLOATS = RS_OFF_TAB + 24;
+extern __shared__ float rs_smem[];  // dynamic shared memory of the resident kernel
+
+// Own nodes on an SBP closure row or column (within 4 nodes of a side of the
+// grid) are updated in a pass of their own; their filter accumulators live
+// here (2 per node, at most RS_SPECIAL_MAX nodes per block).
+constexpr int RS_SPECIAL_MAX = 1400;
+constexpr int RS_OFF_SACC = RS_OFF_TAB + 24;
+constexpr int RS_FLOATS = RS_OFF_SACC + 2 * RS_SPECIAL_MAX;
+
+// Position j of the part of a W x H region outside the rectangle
+// [x0, x1) x [y0, y1) (which may be empty: then y0 = H): rows [0, y0), rows
+// [y1, H), then columns [0, x0) and [x1, W) of the rows between.  It has
+// W H - (x1 - x0)(y1 - y0) positions.
+__device__ __forceinline__ void rs_frame_pos(int j, int W, int H, int x0, int x1, int y0, int y1, int& x, int& y) {
+  const int top = y0 * W;
+  if (j < top) {
+    y = j / W;
+    x = j - y * W;
+    return;
+  }
+  j -= top;
+  const int bot = (H - y1) * W;
+  if (j < bot) {
+    const int r = j / W;
+    y = y1 + r;
+    x = j - r * W;
+    return;
+  }
+  j -= bot;
+  const int sw = x0 + (W - x1);
+  const int r = j / sw, c = j - r * sw;
+  y = y0 + r;
+  x = c < x0 ? c : x1 + (c - x0);
+}
 
 // SBP first derivative as sbp_d1, with the closure rows read from the shared
 // copy `tab`: lanes on different closure rows then read different banks
@@ -890,10 +923,135 @@ __device__ __forceinline__ void walk_next(int& x, int& y, int w, int sx, int sy)
   }
 }
 
+// Stresses at one stress-tile position (qx, qy) of the block at (X0, Y0):
+// the general form (SBP closures; nothing outside the grid).
+__device__ __forceinline__ void rs_stress_gen(const float* __restrict__ lam, const float* __restrict__ mu, int n0,
+                                              int n1, int npx, int X0, int Y0, int obase, int qx, int qy,
+                                              const float* tab) {
+  const int x = X0 + qx - RS_HS, y = Y0 + qy - RS_HS;
+  if (x < 0 || x >= n0 || y < 0 || y >= n1) return;
+  const int o = obase + (qy - RS_HS) * npx + (qx - RS_HS);
+  const float l = __ldg(lam + o), m = __ldg(mu + o);
+  const int pu = (qy + RS_HU - RS_HS) * RS_UX + (qx + RS_HU - RS_HS);
+  const float* U = rs_smem + pu;
+  const float* V = rs_smem + RS_OFF_V + pu;
+  float u_x, v_x, u_y, v_y;
+  if (x < 4 || x > n0 - 5) {
+    u_x = rs_sbp_d1(U, 1, x, n0, tab);
+    v_x = rs_sbp_d1(V, 1, x, n0, tab);
+  } else {
+    u_x = c4(U[-2], U[-1], U[1], U[2]);
+    v_x = c4(V[-2], V[-1], V[1], V[2]);
+  }
+  if (y < 4 || y > n1 - 5) {
+    u_y = rs_sbp_d1(U, RS_UX, y, n1, tab);
+    v_y = rs_sbp_d1(V, RS_UX, y, n1, tab);
+  } else {
+    u_y = c4(U[-2 * RS_UX], U[-RS_UX], U[RS_UX], U[2 * RS_UX]);
+    v_y = c4(V[-2 * RS_UX], V[-RS_UX], V[RS_UX], V[2 * RS_UX]);
+  }
+  const float div = u_x + v_y;
+  const int ps = qy * RS_SX + qx;
+  rs_smem[RS_OFF_XX + ps] = l * div + 2.0f * m * u_x;
+  rs_smem[RS_OFF_YY + ps] = l * div + 2.0f * m * v_y;
+  rs_smem[RS_OFF_XY + ps] = m * (u_y + v_x);
+}
+
+// Per-level scalars of the leapfrog/filter update.
+struct RsLevel {
+  float kt, w0, wnew, cosn;
+  int first;  // level 0: Taylor start
+  int last;   // last level: u^{n+1} is not stored
+};
+
+// -D sigma + H^{-1} B sigma at own node (ix, iy), times 1/(rho h^2), plus the
+// forcing: the general form (SBP closures, boundary terms).
+__device__ __forceinline__ void rs_accel_gen(const Geom& g, const float* __restrict__ irh2,
+                                             const float* __restrict__ frho, int F, int X0, int Y0, int obase, int ix,
+                                             int iy, const RsLevel& L, const float* tab, float& au, float& av) {
+  const int n0 = g.n[0], n1 = g.n[1];
+  const int x = X0 + ix, y = Y0 + iy;
+  const int ps = (iy + RS_HS) * RS_SX + (ix + RS_HS);
+  const float* Sxx = rs_smem + RS_OFF_XX + ps;
+  const float* Syy = rs_smem + RS_OFF_YY + ps;
+  const float* Sxy = rs_smem + RS_OFF_XY + ps;
+  float kxu, kxv, kyu, kyv;
+  if (x < 4 || x > n0 - 5) {
+    kxu = rs_sbp_d1(Sxx, 1, x, n0, tab);
+    kxv = rs_sbp_d1(Sxy, 1, x, n0, tab);
+  } else {
+    kxu = c4(Sxx[-2], Sxx[-1], Sxx[1], Sxx[2]);
+    kxv = c4(Sxy[-2], Sxy[-1], Sxy[1], Sxy[2]);
+  }
+  if (y < 4 || y > n1 - 5) {
+    kyu = rs_sbp_d1(Sxy, RS_SX, y, n1, tab);
+    kyv = rs_sbp_d1(Syy, RS_SX, y, n1, tab);
+  } else {
+    kyu = c4(Sxy[-2 * RS_SX], Sxy[-RS_SX], Sxy[RS_SX], Sxy[2 * RS_SX]);
+    kyv = c4(Syy[-2 * RS_SX], Syy[-RS_SX], Syy[RS_SX], Syy[2 * RS_SX]);
+  }
+  float ku = -kxu - kyu;
+  float kv = -kxv - kyv;
+  const float inv_h0 = 48.0f / 17.0f;
+  if (x == 0) {
+    ku -= inv_h0 * Sxx[0];
+    kv -= inv_h0 * Sxy[0];
+  } else if (x == n0 - 1) {
+    ku += inv_h0 * Sxx[0];
+    kv += inv_h0 * Sxy[0];
+  }
+  if (y == 0) {
+    ku -= inv_h0 * Sxy[0];
+    kv -= inv_h0 * Syy[0];
+  } else if (y == n1 - 1) {
+    ku += inv_h0 * Sxy[0];
+    kv += inv_h0 * Syy[0];
+  }
+  const int o = obase + iy * g.np[0] + ix;
+  const float irh = __ldg(irh2 + o);
+  au = ku * irh;
+  av = kv * irh;
+  if (frho) {
+    au += __ldg(frho + o) * L.cosn;
+    av += __ldg(frho + F + o) * L.cosn;
+  }
+}
+
+// Leapfrog/filter update of own node (ix, iy) from its accelerations (the
+// arithmetic of leapfrog_update in FP32): delta and u in shared memory, the
+// accumulators in acu, acv.
+__device__ __forceinline__ void rs_update(int ix, int iy, float au, float av, const RsLevel& L, float& acu,
+                                          float& acv) {
+  const int pu = (iy + RS_HU) * RS_UX + (ix + RS_HU);
+  const int pd = iy * RS_BXMAX + ix;
+  const float uu = rs_smem[pu], uv = rs_smem[RS_OFF_V + pu];
+  float du, dv;
+  if (L.first) {
+    du = -0.5f * L.kt * au;
+    dv = -0.5f * L.kt * av;
+  } else {
+    du = rs_smem[RS_OFF_DU + pd] - L.kt * au;
+    dv = rs_smem[RS_OFF_DV + pd] - L.kt * av;
+  }
+  const float nu_ = uu + du, nv_ = uv + dv;
+  if (L.first) {
+    acu = L.w0 * uu + L.wnew * nu_;
+    acv = L.w0 * uv + L.wnew * nv_;
+  } else {
+    acu += L.wnew * nu_;
+    acv += L.wnew * nv_;
+  }
+  rs_smem[RS_OFF_DU + pd] = du;
+  rs_smem[RS_OFF_DV + pd] = dv;
+  if (!L.last) {
+    rs_smem[pu] = nu_;
+    rs_smem[RS_OFF_V + pu] = nv_;
+  }
+}
+
 template <int NT, int NK>
 __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShape sh, ResidentIO io) {
   if (g.dim != 2) return;
-  extern __shared__ float rs_smem[];
   __shared__ int s_ok;
   const int n0 = g.n[0], n1 = g.n[1];
   const int cx = blockIdx.x % sh.px;
@@ -907,9 +1065,8 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
   float* const sxx = rs_smem + RS_OFF_XX;
   float* const syy = rs_smem + RS_OFF_YY;
   float* const sxy = rs_smem + RS_OFF_XY;
-  float* const sdu = rs_smem + RS_OFF_DU;
-  float* const sdv = rs_smem + RS_OFF_DV;
   float* const tab = rs_smem + RS_OFF_TAB;
+  float* const sacc = rs_smem + RS_OFF_SACC;
   const int t = threadIdx.x;
   const int F = (int)g.field;  // < 2^31 (checked at creation)
   const int npx = g.np[0];
@@ -917,8 +1074,18 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
   const int ubase = obase - RS_HU * npx - RS_HU;         // ... of u tile position (0, 0)
   const int ux = wx + 2 * RS_HU, uy = wy + 2 * RS_HU;
   const int sxn = wx + 2 * RS_HS, syn = wy + 2 * RS_HS;
-  const int nown = wx * wy;
-  const bool lf0 = g.lo_free[0], hf0 = g.hi_free[0], lf1 = g.lo_free[1], hf1 = g.hi_free[1];
+  // Stress positions on central rows and columns (x and y in [4, n - 5]):
+  // the rectangle [qa, qb) x [ra, rb) of the stress tile; the rest (closure
+  // rows and columns, positions outside the grid) is the stress frame.
+  int qa = max(0, 6 - X0), qb = min(sxn, n0 - 2 - X0), ra = max(0, 6 - Y0), rb = min(syn, n1 - 2 - Y0);
+  if (qb <= qa || rb <= ra) qa = qb = 0, ra = rb = syn;
+  const int wq = qb - qa, nsframe = sxn * syn - wq * (rb - ra);
+  // Own nodes on central rows and columns: the rectangle [xa, xb) x [ya, yb)
+  // of the block (all unknowns, no closure, no boundary term); the others
+  // (within 4 nodes of a side of the grid) are the special nodes.
+  int xa = max(0, 4 - X0), xb = min(wx, n0 - 4 - X0), ya = max(0, 4 - Y0), yb = min(wy, n1 - 4 - Y0);
+  if (xb <= xa || yb <= ya) xa = xb = 0, ya = yb = wy;
+  const int wr = xb - xa, nreg = wr * (yb - ya), nspec = wx * wy - nreg;
   if (t < 24) tab[t] = c_sbp_f[t / 6][t % 6];
 
   {  // u^0 on the whole tile
@@ -930,179 +1097,152 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
       sv[ly * RS_UX + lx] = __ldcg(io.u0 + F + o);
     }
   }
-  // walk of this thread's own nodes: l = t + NT k -> (ix, iy)
-  const int ix0 = t % wx, iy0 = t / wx;
-  const int qstep = NT / wx, rstep = NT % wx;
+  // walk of this thread's regular nodes: l = t + NT k -> (xa + l % wr, ya + l / wr);
+  // (ix, iy) below are relative to (xa, ya)
+  const int wrs = max(wr, 1);
+  const int ix0 = t % wrs, iy0 = t / wrs;
+  const int qstep = NT / wrs, rstep = NT % wrs;
   float ac0[NK], ac1[NK];
 #pragma unroll
   for (int k = 0; k < NK; ++k) ac0[k] = ac1[k] = 0.f;
-  const float kt = (float)io.kt, w0 = (float)io.w0;
-  const float inv_h0 = 48.0f / 17.0f;
+  RsLevel L;
+  L.kt = (float)io.kt;
+  L.w0 = (float)io.w0;
   bool alive = true;
   __syncthreads();
 
   for (int n = 0; n < io.nsteps; ++n) {
     if (n > 0) {  // halo ring of u^n from the neighbours' rims
-      const float* xb = (n & 1) ? io.xbuf1 : io.xbuf0;
+      const float* xbuf = (n & 1) ? io.xbuf1 : io.xbuf0;
       {  // top and bottom strips: tile rows 0..3 and wy+4..wy+7, all columns
         int lx = t % ux, r = t / ux;
         const int rx = NT % ux, ry = NT / ux;
         for (; r < 2 * RS_HU; walk_next(lx, r, ux, rx, ry)) {
           const int ly = r < RS_HU ? r : wy + r;
           const int o = ubase + ly * npx + lx;
-          su[ly * RS_UX + lx] = __ldcg(xb + o);
-          sv[ly * RS_UX + lx] = __ldcg(xb + F + o);
+          su[ly * RS_UX + lx] = __ldcg(xbuf + o);
+          sv[ly * RS_UX + lx] = __ldcg(xbuf + F + o);
         }
       }
       for (int i = t; i < 2 * RS_HU * wy; i += NT) {  // side strips: columns 0..3 and wx+4..wx+7
         const int c = i & (2 * RS_HU - 1), ly = RS_HU + (i >> 3);
         const int lx = c < RS_HU ? c : wx + c;
         const int o = ubase + ly * npx + lx;
-        su[ly * RS_UX + lx] = __ldcg(xb + o);
-        sv[ly * RS_UX + lx] = __ldcg(xb + F + o);
+        su[ly * RS_UX + lx] = __ldcg(xbuf + o);
+        sv[ly * RS_UX + lx] = __ldcg(xbuf + F + o);
       }
       __syncthreads();
     }
-    {  // stresses on the block +- 2 (inside the grid)
-      int qx = t % sxn, qy = t / sxn;
-      const int rx = NT % sxn, ry = NT / sxn;
-      for (; qy < syn; walk_next(qx, qy, sxn, rx, ry)) {
-        const int x = X0 + qx - RS_HS, y = Y0 + qy - RS_HS;
-        if (x < 0 || x >= n0 || y < 0 || y >= n1) continue;
-        const int o = obase + (qy - RS_HS) * npx + (qx - RS_HS);
+    if (wq > 0) {  // stresses on central positions: no closure, no bounds
+      int qx = t % wq, qy = ra + t / wq;
+      const int rx = NT % wq, ry = NT / wq;
+      for (; qy < rb; walk_next(qx, qy, wq, rx, ry)) {
+        const int px_ = qa + qx;
+        const int o = obase + (qy - RS_HS) * npx + (px_ - RS_HS);
         const float l = __ldg(io.lam + o), m = __ldg(io.mu + o);
-        const int pu = (qy + RS_HU - RS_HS) * RS_UX + (qx + RS_HU - RS_HS);
+        const int pu = (qy + RS_HU - RS_HS) * RS_UX + (px_ + RS_HU - RS_HS);
         const float* U = su + pu;
         const float* V = sv + pu;
-        float u_x, v_x, u_y, v_y;
-        if (x < 4 || x > n0 - 5) {
-          u_x = rs_sbp_d1(U, 1, x, n0, tab);
-          v_x = rs_sbp_d1(V, 1, x, n0, tab);
-        } else {
-          u_x = c4(U[-2], U[-1], U[1], U[2]);
-          v_x = c4(V[-2], V[-1], V[1], V[2]);
-        }
-        if (y < 4 || y > n1 - 5) {
-          u_y = rs_sbp_d1(U, RS_UX, y, n1, tab);
-          v_y = rs_sbp_d1(V, RS_UX, y, n1, tab);
-        } else {
-          u_y = c4(U[-2 * RS_UX], U[-RS_UX], U[RS_UX], U[2 * RS_UX]);
-          v_y = c4(V[-2 * RS_UX], V[-RS_UX], V[RS_UX], V[2 * RS_UX]);
-        }
+        const float u_x = c4(U[-2], U[-1], U[1], U[2]);
+        const float v_x = c4(V[-2], V[-1], V[1], V[2]);
+        const float u_y = c4(U[-2 * RS_UX], U[-RS_UX], U[RS_UX], U[2 * RS_UX]);
+        const float v_y = c4(V[-2 * RS_UX], V[-RS_UX], V[RS_UX], V[2 * RS_UX]);
         const float div = u_x + v_y;
-        const int ps = qy * RS_SX + qx;
+        const int ps = qy * RS_SX + px_;
         sxx[ps] = l * div + 2.0f * m * u_x;
         syy[ps] = l * div + 2.0f * m * v_y;
         sxy[ps] = m * (u_y + v_x);
       }
     }
+    for (int j = t; j < nsframe; j += NT) {  // the stress frame: general form
+      int qx, qy;
+      rs_frame_pos(j, sxn, syn, qa, qb, ra, rb, qx, qy);
+      rs_stress_gen(io.lam, io.mu, n0, n1, npx, X0, Y0, obase, qx, qy, tab);
+    }
     __syncthreads();
     // divergence and leapfrog/filter update of the own nodes
-    const bool last = n == io.nsteps - 1;
-    const float cosn = (float)io.cosn[n], wnew = (float)io.wnew[n];
+    L.first = n == 0;
+    L.last = n == io.nsteps - 1;
+    L.cosn = (float)io.cosn[n];
+    L.wnew = (float)io.wnew[n];
     float* xo = (n & 1) ? io.xbuf0 : io.xbuf1;  // rims of u^{n+1}
     int ix = ix0, iy = iy0;
 #pragma unroll
-    for (int k = 0; k < NK; ++k) {
-      if (t + k * NT < nown) {
-        const int x = X0 + ix, y = Y0 + iy;
-        const int pu = (iy + RS_HU) * RS_UX + (ix + RS_HU);
-        const bool unk = (x > 0 || lf0) && (x < n0 - 1 || hf0) && (y > 0 || lf1) && (y < n1 - 1 || hf1);
-        if (unk) {
-          const int ps = (iy + RS_HS) * RS_SX + (ix + RS_HS);
-          const float* Sxx = sxx + ps;
-          const float* Syy = syy + ps;
-          const float* Sxy = sxy + ps;
-          float kxu, kxv, kyu, kyv;
-          if (x < 4 || x > n0 - 5) {
-            kxu = rs_sbp_d1(Sxx, 1, x, n0, tab);
-            kxv = rs_sbp_d1(Sxy, 1, x, n0, tab);
-          } else {
-            kxu = c4(Sxx[-2], Sxx[-1], Sxx[1], Sxx[2]);
-            kxv = c4(Sxy[-2], Sxy[-1], Sxy[1], Sxy[2]);
-          }
-          if (y < 4 || y > n1 - 5) {
-            kyu = rs_sbp_d1(Sxy, RS_SX, y, n1, tab);
-            kyv = rs_sbp_d1(Syy, RS_SX, y, n1, tab);
-          } else {
-            kyu = c4(Sxy[-2 * RS_SX], Sxy[-RS_SX], Sxy[RS_SX], Sxy[2 * RS_SX]);
-            kyv = c4(Syy[-2 * RS_SX], Syy[-RS_SX], Syy[RS_SX], Syy[2 * RS_SX]);
-          }
-          float ku = -kxu - kyu;
-          float kv = -kxv - kyv;
-          if (x == 0) {
-            ku -= inv_h0 * Sxx[0];
-            kv -= inv_h0 * Sxy[0];
-          } else if (x == n0 - 1) {
-            ku += inv_h0 * Sxx[0];
-            kv += inv_h0 * Sxy[0];
-          }
-          if (y == 0) {
-            ku -= inv_h0 * Sxy[0];
-            kv -= inv_h0 * Syy[0];
-          } else if (y == n1 - 1) {
-            ku += inv_h0 * Sxy[0];
-            kv += inv_h0 * Syy[0];
-          }
-          const int o = obase + iy * npx + ix;
-          const float irh = __ldg(io.irh2 + o);
-          float au = ku * irh, av = kv * irh;
-          if (io.frho) {
-            au += __ldg(io.frho + o) * cosn;
-            av += __ldg(io.frho + F + o) * cosn;
-          }
-          const int pd = iy * RS_BXMAX + ix;
-          const float uu = su[pu], uv = sv[pu];
-          float du, dv;
-          if (n == 0) {
-            du = -0.5f * kt * au;
-            dv = -0.5f * kt * av;
-          } else {
-            du = sdu[pd] - kt * au;
-            dv = sdv[pd] - kt * av;
-          }
-          const float nu_ = uu + du, nv_ = uv + dv;
-          if (n == 0) {
-            ac0[k] = w0 * uu + wnew * nu_;
-            ac1[k] = w0 * uv + wnew * nv_;
-          } else {
-            ac0[k] += wnew * nu_;
-            ac1[k] += wnew * nv_;
-          }
-          sdu[pd] = du;
-          sdv[pd] = dv;
-          if (!last) {
-            su[pu] = nu_;
-            sv[pu] = nv_;
-          }
+    for (int k = 0; k < NK; ++k) {  // regular nodes: central differences only
+      if (t + k * NT < nreg) {
+        const int jx = xa + ix, jy = ya + iy;
+        const int ps = (jy + RS_HS) * RS_SX + (jx + RS_HS);
+        const float* Sxx = sxx + ps;
+        const float* Syy = syy + ps;
+        const float* Sxy = sxy + ps;
+        const float kxu = c4(Sxx[-2], Sxx[-1], Sxx[1], Sxx[2]);
+        const float kxv = c4(Sxy[-2], Sxy[-1], Sxy[1], Sxy[2]);
+        const float kyu = c4(Sxy[-2 * RS_SX], Sxy[-RS_SX], Sxy[RS_SX], Sxy[2 * RS_SX]);
+        const float kyv = c4(Syy[-2 * RS_SX], Syy[-RS_SX], Syy[RS_SX], Syy[2 * RS_SX]);
+        const float ku = -kxu - kyu;
+        const float kv = -kxv - kyv;
+        const int o = obase + jy * npx + jx;
+        const float irh = __ldg(io.irh2 + o);
+        float au = ku * irh, av = kv * irh;
+        if (io.frho) {
+          au += __ldg(io.frho + o) * L.cosn;
+          av += __ldg(io.frho + F + o) * L.cosn;
         }
-        if (!last && (ix < RS_HU || ix >= wx - RS_HU || iy < RS_HU || iy >= wy - RS_HU)) {
-          const int o = obase + iy * npx + ix;
+        rs_update(jx, jy, au, av, L, ac0[k], ac1[k]);
+        if (!L.last && (jx < RS_HU || jx >= wx - RS_HU || jy < RS_HU || jy >= wy - RS_HU)) {
+          const int pu = (jy + RS_HU) * RS_UX + (jx + RS_HU);
           xo[o] = su[pu];
           xo[F + o] = sv[pu];
         }
       }
-      walk_next(ix, iy, wx, rstep, qstep);
+      walk_next(ix, iy, wr, rstep, qstep);
     }
-    if (!last && !rs_grid_barrier(io.bar, (unsigned)(n + 1) * gridDim.x, &s_ok)) {
+    for (int j = t; j < nspec; j += NT) {  // special nodes: general form, accumulators in shared memory
+      int jx, jy;
+      rs_frame_pos(j, wx, wy, xa, xb, ya, yb, jx, jy);
+      const int x = X0 + jx, y = Y0 + jy;
+      const bool unk = (x > 0 || g.lo_free[0]) && (x < n0 - 1 || g.hi_free[0]) && (y > 0 || g.lo_free[1]) &&
+                       (y < n1 - 1 || g.hi_free[1]);
+      if (unk) {
+        float au, av;
+        rs_accel_gen(g, io.irh2, io.frho, F, X0, Y0, obase, jx, jy, L, tab, au, av);
+        rs_update(jx, jy, au, av, L, sacc[2 * j], sacc[2 * j + 1]);
+      }
+      if (!L.last && (jx < RS_HU || jx >= wx - RS_HU || jy < RS_HU || jy >= wy - RS_HU)) {
+        const int o = obase + jy * npx + jx;
+        const int pu = (jy + RS_HU) * RS_UX + (jx + RS_HU);
+        xo[o] = su[pu];
+        xo[F + o] = sv[pu];
+      }
+    }
+    if (!L.last && !rs_grid_barrier(io.bar, (unsigned)(n + 1) * gridDim.x, &s_ok)) {
       alive = false;
       break;
     }
   }
-  // accumulator of the own unknowns (NaN when the barrier gave up)
+  // accumulators of the own unknowns (NaN when the barrier gave up)
   const float nanv = __int_as_float(0x7fc00000);
   int ix = ix0, iy = iy0;
 #pragma unroll
   for (int k = 0; k < NK; ++k) {
-    if (t + k * NT < nown) {
-      const int x = X0 + ix, y = Y0 + iy;
-      if ((x > 0 || lf0) && (x < n0 - 1 || hf0) && (y > 0 || lf1) && (y < n1 - 1 || hf1)) {
-        const int o = obase + iy * npx + ix;
-        io.acc[o] = alive ? ac0[k] : nanv;
-        io.acc[F + o] = alive ? ac1[k] : nanv;
-      }
+    if (t + k * NT < nreg) {
+      const int o = obase + (ya + iy) * npx + (xa + ix);
+      io.acc[o] = alive ? ac0[k] : nanv;
+      io.acc[F + o] = alive ? ac1[k] : nanv;
     }
-    walk_next(ix, iy, wx, rstep, qstep);
+    walk_next(ix, iy, wr, rstep, qstep);
+  }
+  __syncthreads();  // the special accumulators were written by other threads
+  for (int j = t; j < nspec; j += NT) {
+    int jx, jy;
+    rs_frame_pos(j, wx, wy, xa, xb, ya, yb, jx, jy);
+    const int x = X0 + jx, y = Y0 + jy;
+    if ((x > 0 || g.lo_free[0]) && (x < n0 - 1 || g.hi_free[0]) && (y > 0 || g.lo_free[1]) &&
+        (y < n1 - 1 || g.hi_free[1])) {
+      const int o = obase + jy * npx + jx;
+      io.acc[o] = alive ? sacc[2 * j] : nanv;
+      io.acc[F + o] = alive ? sacc[2 * j + 1] : nanv;
+    }
   }
 }
 
@@ -1167,6 +1307,20 @@ ResidentPlan plan_resident_o4(const Geom& g, int shape) {
       const int pya = (n1 + by - 1) / by;
       if (n1 - (pya - 1) * by < 8) continue;
       if ((long long)wmax * by > cap || by > RS_BYMAX) continue;
+      // nodes within 4 of a side of the grid, per block, fit their shared accumulators
+      auto spec = [&](int X0, int w, int Y0, int h) {
+        const int a = std::max(0, 4 - X0), b = std::min(w, n0 - 4 - X0);
+        const int c = std::max(0, 4 - Y0), d = std::min(h, n1 - 4 - Y0);
+        return w * h - ((b > a && d > c) ? (b - a) * (d - c) : 0);
+      };
+      bool fits = true;
+      for (int cy = 0; cy < pya && fits; ++cy)
+        for (int cx = 0; cx < px && fits; ++cx) {
+          const int X0 = cx == 0 ? 0 : ex + (cx - 1) * bx;
+          const int w = cx == 0 ? ex : std::min(bx, n0 - X0);
+          fits = spec(X0, w, cy * by, std::min(by, n1 - cy * by)) <= RS_SPECIAL_MAX;
+        }
+      if (!fits) continue;
       const size_t sm = resident_smem();
       if (sm > (size_t)smem_max) continue;
       // per-CTA work (u tile + stress tile) of the slowest block
