@@ -136,10 +136,10 @@ cudaError_t launch_fill_mass(const Geom& g, int order, const double* rho_full, d
 // Order 4 (SBP), 2D, FP32, one right-hand side: all nt*periods time levels in
 // one cooperative launch, one CTA per SM, each owning a bx x by block of
 // nodes whose state stays in shared memory and registers.  Shapes: threads
-// per CTA x own nodes per thread at most.
+// per CTA x pairs of regular own nodes (adjacent along x) per thread at most.
 constexpr int RS_SHAPES = 3;
 constexpr int RS_SHAPE_THREADS[RS_SHAPES] = {1024, 768, 512};
-constexpr int RS_SHAPE_NODES[RS_SHAPES] = {7, 9, 14};
+constexpr int RS_SHAPE_PAIRS[RS_SHAPES] = {4, 5, 7};
 struct ResidentPlan {
   int ok = 0;
   int shape = 0;       // index into RS_SHAPE_*

@@ -767,11 +767,16 @@ cudaError_t launch_minvK(const Geom& g, int order, const T* u, T* out, const T* 
 // solve in ONE cooperative launch with the state held on chip.
 //
 // One CTA of NT threads per SM owns a wx x wy block of nodes (every block
-// at least 8 x 8, so SBP closure reaches stay inside the halos).  It keeps
+// at least 8 x 8, so SBP closure reaches stay inside the halos).  Its nodes
+// on central rows and columns (x, y in [4, n - 5]) form a rectangle, done in
+// pairs along x with no per-node test; the others (within 4 nodes of a side:
+// SBP closures, boundary terms, Dirichlet nodes) are special and take a pass
+// of their own with the general code.  The CTA keeps
 //   in shared memory: u on the block +- 4 nodes, the stresses on the block
-//                     +- 2 nodes, delta on the block;
-//   in registers:     the filter accumulator of its nodes (node t + NT k of
-//                     the block for thread t, k < NK).
+//                     +- 2 nodes, delta on the block, the special nodes'
+//                     filter accumulators;
+//   in registers:     the filter accumulators of its regular node pairs
+//                     (pair t + NT k of the rectangle for thread t, k < NP).
 // Per time level a CTA reloads only the 4-node halo ring of u (its
 // neighbours' rims, written at the previous level to a global exchange
 // buffer), recomputes the stresses on block +- 2 from u on block +- 4, forms
@@ -1049,7 +1054,7 @@ __device__ __forceinline__ void rs_update(int ix, int iy, float au, float av, co
   }
 }
 
-template <int NT, int NK>
+template <int NT, int NP>
 __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShape sh, ResidentIO io) {
   if (g.dim != 2) return;
   __shared__ int s_ok;
@@ -1079,13 +1084,18 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
   // rows and columns, positions outside the grid) is the stress frame.
   int qa = max(0, 6 - X0), qb = min(sxn, n0 - 2 - X0), ra = max(0, 6 - Y0), rb = min(syn, n1 - 2 - Y0);
   if (qb <= qa || rb <= ra) qa = qb = 0, ra = rb = syn;
+  qb = qa + ((qb - qa) & ~1);  // even width: the rectangle is done in pairs of positions
+  if (qb == qa) ra = rb = syn;
   const int wq = qb - qa, nsframe = sxn * syn - wq * (rb - ra);
   // Own nodes on central rows and columns: the rectangle [xa, xb) x [ya, yb)
   // of the block (all unknowns, no closure, no boundary term); the others
   // (within 4 nodes of a side of the grid) are the special nodes.
   int xa = max(0, 4 - X0), xb = min(wx, n0 - 4 - X0), ya = max(0, 4 - Y0), yb = min(wy, n1 - 4 - Y0);
   if (xb <= xa || yb <= ya) xa = xb = 0, ya = yb = wy;
+  xb = xa + ((xb - xa) & ~1);  // even width: regular nodes are updated in pairs
+  if (xb == xa) ya = yb = wy;
   const int wr = xb - xa, nreg = wr * (yb - ya), nspec = wx * wy - nreg;
+  const int wr2 = wr >> 1, npair = nreg >> 1;
   if (t < 24) tab[t] = c_sbp_f[t / 6][t % 6];
 
   {  // u^0 on the whole tile
@@ -1097,14 +1107,14 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
       sv[ly * RS_UX + lx] = __ldcg(io.u0 + F + o);
     }
   }
-  // walk of this thread's regular nodes: l = t + NT k -> (xa + l % wr, ya + l / wr);
-  // (ix, iy) below are relative to (xa, ya)
-  const int wrs = max(wr, 1);
+  // walk of this thread's regular node pairs: l = t + NT k -> (xa + 2 (l % wr2), ya + l / wr2);
+  // (ip, iy) below are relative to (xa / 2, ya)
+  const int wrs = max(wr2, 1);
   const int ix0 = t % wrs, iy0 = t / wrs;
   const int qstep = NT / wrs, rstep = NT % wrs;
-  float ac0[NK], ac1[NK];
+  float ac0[NP], ac1[NP], ac2[NP], ac3[NP];  // u, v of the pair's first node; u, v of its second
 #pragma unroll
-  for (int k = 0; k < NK; ++k) ac0[k] = ac1[k] = 0.f;
+  for (int k = 0; k < NP; ++k) ac0[k] = ac1[k] = ac2[k] = ac3[k] = 0.f;
   RsLevel L;
   L.kt = (float)io.kt;
   L.w0 = (float)io.w0;
@@ -1133,25 +1143,32 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
       }
       __syncthreads();
     }
-    if (wq > 0) {  // stresses on central positions: no closure, no bounds
-      int qx = t % wq, qy = ra + t / wq;
-      const int rx = NT % wq, ry = NT / wq;
-      for (; qy < rb; walk_next(qx, qy, wq, rx, ry)) {
-        const int px_ = qa + qx;
-        const int o = obase + (qy - RS_HS) * npx + (px_ - RS_HS);
-        const float l = __ldg(io.lam + o), m = __ldg(io.mu + o);
-        const int pu = (qy + RS_HU - RS_HS) * RS_UX + (px_ + RS_HU - RS_HS);
-        const float* U = su + pu;
-        const float* V = sv + pu;
-        const float u_x = c4(U[-2], U[-1], U[1], U[2]);
-        const float v_x = c4(V[-2], V[-1], V[1], V[2]);
-        const float u_y = c4(U[-2 * RS_UX], U[-RS_UX], U[RS_UX], U[2 * RS_UX]);
-        const float v_y = c4(V[-2 * RS_UX], V[-RS_UX], V[RS_UX], V[2 * RS_UX]);
-        const float div = u_x + v_y;
-        const int ps = qy * RS_SX + px_;
-        sxx[ps] = l * div + 2.0f * m * u_x;
-        syy[ps] = l * div + 2.0f * m * v_y;
-        sxy[ps] = m * (u_y + v_x);
+    if (wq > 0) {  // stresses on central positions, two per thread (8-byte shared accesses)
+      const int wp = wq >> 1;
+      int pp = t % wp, qy = ra + t / wp;
+      const int rx = NT % wp, ry = NT / wp;
+      constexpr int RU = RS_UX / 2;
+      for (; qy < rb; walk_next(pp, qy, wp, rx, ry)) {
+        const int qx = qa + 2 * pp;
+        const int o = obase + (qy - RS_HS) * npx + (qx - RS_HS);
+        const float l0 = __ldg(io.lam + o), l1 = __ldg(io.lam + o + 1);
+        const float m0 = __ldg(io.mu + o), m1 = __ldg(io.mu + o + 1);
+        const int pu = (qy + RS_HU - RS_HS) * RS_UX + (qx + RS_HU - RS_HS);  // even
+        const float2* U = reinterpret_cast<const float2*>(su + pu);
+        const float2* V = reinterpret_cast<const float2*>(sv + pu);
+        const float2 ua = U[-1], ub = U[0], uc = U[1];
+        const float2 va = V[-1], vb = V[0], vc = V[1];
+        const float ux0 = c4(ua.x, ua.y, ub.y, uc.x), ux1 = c4(ua.y, ub.x, uc.x, uc.y);
+        const float vx0 = c4(va.x, va.y, vb.y, vc.x), vx1 = c4(va.y, vb.x, vc.x, vc.y);
+        const float2 um2 = U[-2 * RU], um1 = U[-RU], up1 = U[RU], up2 = U[2 * RU];
+        const float2 vm2 = V[-2 * RU], vm1 = V[-RU], vp1 = V[RU], vp2 = V[2 * RU];
+        const float uy0 = c4(um2.x, um1.x, up1.x, up2.x), uy1 = c4(um2.y, um1.y, up1.y, up2.y);
+        const float vy0 = c4(vm2.x, vm1.x, vp1.x, vp2.x), vy1 = c4(vm2.y, vm1.y, vp1.y, vp2.y);
+        const float div0 = ux0 + vy0, div1 = ux1 + vy1;
+        const int ps = qy * RS_SX + qx;  // even
+        *reinterpret_cast<float2*>(sxx + ps) = make_float2(l0 * div0 + 2.0f * m0 * ux0, l1 * div1 + 2.0f * m1 * ux1);
+        *reinterpret_cast<float2*>(syy + ps) = make_float2(l0 * div0 + 2.0f * m0 * vy0, l1 * div1 + 2.0f * m1 * vy1);
+        *reinterpret_cast<float2*>(sxy + ps) = make_float2(m0 * (uy0 + vx0), m1 * (uy1 + vx1));
       }
     }
     for (int j = t; j < nsframe; j += NT) {  // the stress frame: general form
@@ -1168,34 +1185,78 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
     float* xo = (n & 1) ? io.xbuf0 : io.xbuf1;  // rims of u^{n+1}
     int ix = ix0, iy = iy0;
 #pragma unroll
-    for (int k = 0; k < NK; ++k) {  // regular nodes: central differences only
-      if (t + k * NT < nreg) {
-        const int jx = xa + ix, jy = ya + iy;
-        const int ps = (jy + RS_HS) * RS_SX + (jx + RS_HS);
-        const float* Sxx = sxx + ps;
-        const float* Syy = syy + ps;
-        const float* Sxy = sxy + ps;
-        const float kxu = c4(Sxx[-2], Sxx[-1], Sxx[1], Sxx[2]);
-        const float kxv = c4(Sxy[-2], Sxy[-1], Sxy[1], Sxy[2]);
-        const float kyu = c4(Sxy[-2 * RS_SX], Sxy[-RS_SX], Sxy[RS_SX], Sxy[2 * RS_SX]);
-        const float kyv = c4(Syy[-2 * RS_SX], Syy[-RS_SX], Syy[RS_SX], Syy[2 * RS_SX]);
-        const float ku = -kxu - kyu;
-        const float kv = -kxv - kyv;
+    for (int k = 0; k < NP; ++k) {  // regular node pairs: central differences only
+      if (t + k * NT < npair) {
+        const int jx = xa + 2 * ix, jy = ya + iy;
+        const int ps = (jy + RS_HS) * RS_SX + (jx + RS_HS);  // even
+        const float2* SXX = reinterpret_cast<const float2*>(sxx + ps);
+        const float2* SYY = reinterpret_cast<const float2*>(syy + ps);
+        const float2* SXY = reinterpret_cast<const float2*>(sxy + ps);
+        constexpr int RS2 = RS_SX / 2;
+        const float2 xa_ = SXX[-1], xb_ = SXX[0], xc_ = SXX[1];
+        const float2 ya_ = SXY[-1], yb_ = SXY[0], yc_ = SXY[1];
+        const float kxu0 = c4(xa_.x, xa_.y, xb_.y, xc_.x), kxu1 = c4(xa_.y, xb_.x, xc_.x, xc_.y);
+        const float kxv0 = c4(ya_.x, ya_.y, yb_.y, yc_.x), kxv1 = c4(ya_.y, yb_.x, yc_.x, yc_.y);
+        const float2 sm2 = SXY[-2 * RS2], sm1 = SXY[-RS2], sp1 = SXY[RS2], sp2 = SXY[2 * RS2];
+        const float2 tm2 = SYY[-2 * RS2], tm1 = SYY[-RS2], tp1 = SYY[RS2], tp2 = SYY[2 * RS2];
+        const float kyu0 = c4(sm2.x, sm1.x, sp1.x, sp2.x), kyu1 = c4(sm2.y, sm1.y, sp1.y, sp2.y);
+        const float kyv0 = c4(tm2.x, tm1.x, tp1.x, tp2.x), kyv1 = c4(tm2.y, tm1.y, tp1.y, tp2.y);
+        const float ku0 = -kxu0 - kyu0, ku1 = -kxu1 - kyu1;
+        const float kv0 = -kxv0 - kyv0, kv1 = -kxv1 - kyv1;
         const int o = obase + jy * npx + jx;
-        const float irh = __ldg(io.irh2 + o);
-        float au = ku * irh, av = kv * irh;
+        const float r0 = __ldg(io.irh2 + o), r1 = __ldg(io.irh2 + o + 1);
+        float au0 = ku0 * r0, av0 = kv0 * r0, au1 = ku1 * r1, av1 = kv1 * r1;
         if (io.frho) {
-          au += __ldg(io.frho + o) * L.cosn;
-          av += __ldg(io.frho + F + o) * L.cosn;
+          au0 += __ldg(io.frho + o) * L.cosn;
+          au1 += __ldg(io.frho + o + 1) * L.cosn;
+          av0 += __ldg(io.frho + F + o) * L.cosn;
+          av1 += __ldg(io.frho + F + o + 1) * L.cosn;
         }
-        rs_update(jx, jy, au, av, L, ac0[k], ac1[k]);
-        if (!L.last && (jx < RS_HU || jx >= wx - RS_HU || jy < RS_HU || jy >= wy - RS_HU)) {
-          const int pu = (jy + RS_HU) * RS_UX + (jx + RS_HU);
-          xo[o] = su[pu];
-          xo[F + o] = sv[pu];
+        const int pu = (jy + RS_HU) * RS_UX + (jx + RS_HU);  // even
+        const int pd = jy * RS_BXMAX + jx;                   // even
+        float2* Up = reinterpret_cast<float2*>(su + pu);
+        float2* Vp = reinterpret_cast<float2*>(sv + pu);
+        float2* Dup = reinterpret_cast<float2*>(rs_smem + RS_OFF_DU + pd);
+        float2* Dvp = reinterpret_cast<float2*>(rs_smem + RS_OFF_DV + pd);
+        const float2 uu = *Up, uv = *Vp;
+        float2 du, dv;
+        if (L.first) {
+          du = make_float2(-0.5f * L.kt * au0, -0.5f * L.kt * au1);
+          dv = make_float2(-0.5f * L.kt * av0, -0.5f * L.kt * av1);
+        } else {
+          const float2 d0 = *Dup, d1 = *Dvp;
+          du = make_float2(d0.x - L.kt * au0, d0.y - L.kt * au1);
+          dv = make_float2(d1.x - L.kt * av0, d1.y - L.kt * av1);
+        }
+        const float2 nu_ = make_float2(uu.x + du.x, uu.y + du.y), nv_ = make_float2(uv.x + dv.x, uv.y + dv.y);
+        if (L.first) {
+          ac0[k] = L.w0 * uu.x + L.wnew * nu_.x;
+          ac1[k] = L.w0 * uv.x + L.wnew * nv_.x;
+          ac2[k] = L.w0 * uu.y + L.wnew * nu_.y;
+          ac3[k] = L.w0 * uv.y + L.wnew * nv_.y;
+        } else {
+          ac0[k] += L.wnew * nu_.x;
+          ac1[k] += L.wnew * nv_.x;
+          ac2[k] += L.wnew * nu_.y;
+          ac3[k] += L.wnew * nv_.y;
+        }
+        *Dup = du;
+        *Dvp = dv;
+        if (!L.last) {
+          *Up = nu_;
+          *Vp = nv_;
+          const bool rowrim = jy < RS_HU || jy >= wy - RS_HU;
+          if (rowrim || jx < RS_HU || jx >= wx - RS_HU) {
+            xo[o] = nu_.x;
+            xo[F + o] = nv_.x;
+          }
+          if (rowrim || jx + 1 < RS_HU || jx + 1 >= wx - RS_HU) {
+            xo[o + 1] = nu_.y;
+            xo[F + o + 1] = nv_.y;
+          }
         }
       }
-      walk_next(ix, iy, wr, rstep, qstep);
+      walk_next(ix, iy, wr2, rstep, qstep);
     }
     for (int j = t; j < nspec; j += NT) {  // special nodes: general form, accumulators in shared memory
       int jx, jy;
@@ -1224,13 +1285,15 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
   const float nanv = __int_as_float(0x7fc00000);
   int ix = ix0, iy = iy0;
 #pragma unroll
-  for (int k = 0; k < NK; ++k) {
-    if (t + k * NT < nreg) {
-      const int o = obase + (ya + iy) * npx + (xa + ix);
+  for (int k = 0; k < NP; ++k) {
+    if (t + k * NT < npair) {
+      const int o = obase + (ya + iy) * npx + (xa + 2 * ix);
       io.acc[o] = alive ? ac0[k] : nanv;
       io.acc[F + o] = alive ? ac1[k] : nanv;
+      io.acc[o + 1] = alive ? ac2[k] : nanv;
+      io.acc[F + o + 1] = alive ? ac3[k] : nanv;
     }
-    walk_next(ix, iy, wr, rstep, qstep);
+    walk_next(ix, iy, wr2, rstep, qstep);
   }
   __syncthreads();  // the special accumulators were written by other threads
   for (int j = t; j < nspec; j += NT) {
@@ -1251,23 +1314,23 @@ static size_t resident_smem() { return sizeof(float) * (size_t)RS_FLOATS; }
 // Opt the kernel in to the device's largest dynamic shared memory (the same
 // value for every context, so plans of different sizes never undo each
 // other; set before any launch or capture) and report CTAs per SM at smem.
-template <int NT, int NK>
+template <int NT, int NP>
 static cudaError_t resident_prepare(int smem_max, size_t smem, int* per_sm) {
   cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, step2d_o4_resident<NT, NK>);
+  cudaError_t e = cudaFuncGetAttributes(&fa, step2d_o4_resident<NT, NP>);
   if (e != cudaSuccess) return e;
   const int dyn_max = smem_max - (int)fa.sharedSizeBytes;  // static + dynamic <= opt-in limit
   if ((long long)smem > dyn_max) return cudaErrorInvalidValue;
-  e = cudaFuncSetAttribute(step2d_o4_resident<NT, NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+  e = cudaFuncSetAttribute(step2d_o4_resident<NT, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step2d_o4_resident<NT, NK>, NT, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step2d_o4_resident<NT, NP>, NT, smem);
 }
 
 static cudaError_t resident_prepare_shape(int shape, int smem_max, size_t smem, int* per_sm) {
   switch (shape) {
-    case 0: return resident_prepare<RS_SHAPE_THREADS[0], RS_SHAPE_NODES[0]>(smem_max, smem, per_sm);
-    case 1: return resident_prepare<RS_SHAPE_THREADS[1], RS_SHAPE_NODES[1]>(smem_max, smem, per_sm);
-    case 2: return resident_prepare<RS_SHAPE_THREADS[2], RS_SHAPE_NODES[2]>(smem_max, smem, per_sm);
+    case 0: return resident_prepare<RS_SHAPE_THREADS[0], RS_SHAPE_PAIRS[0]>(smem_max, smem, per_sm);
+    case 1: return resident_prepare<RS_SHAPE_THREADS[1], RS_SHAPE_PAIRS[1]>(smem_max, smem, per_sm);
+    case 2: return resident_prepare<RS_SHAPE_THREADS[2], RS_SHAPE_PAIRS[2]>(smem_max, smem, per_sm);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1283,7 +1346,7 @@ ResidentPlan plan_resident_o4(const Geom& g, int shape) {
     cudaGetLastError();
     return best;
   }
-  const long long cap = (long long)RS_SHAPE_THREADS[shape] * RS_SHAPE_NODES[shape];
+  const long long cap = 2LL * RS_SHAPE_THREADS[shape] * RS_SHAPE_PAIRS[shape];
   const int n0 = g.n[0], n1 = g.n[1];
   // Blocks that hold x-closure columns (the first and last along x) take
   // about RS_EDGE_COST longer per node (a few lanes of their warps diverge):
@@ -1309,7 +1372,7 @@ ResidentPlan plan_resident_o4(const Geom& g, int shape) {
       if ((long long)wmax * by > cap || by > RS_BYMAX) continue;
       // nodes within 4 of a side of the grid, per block, fit their shared accumulators
       auto spec = [&](int X0, int w, int Y0, int h) {
-        const int a = std::max(0, 4 - X0), b = std::min(w, n0 - 4 - X0);
+        const int a = std::max(0, 4 - X0), b0 = std::min(w, n0 - 4 - X0), b = b0 > a ? a + ((b0 - a) & ~1) : b0;
         const int c = std::max(0, 4 - Y0), d = std::min(h, n1 - 4 - Y0);
         return w * h - ((b > a && d > c) ? (b - a) * (d - c) : 0);
       };
@@ -1358,7 +1421,7 @@ ResidentPlan plan_resident_o4(const Geom& g, int shape) {
   return best;
 }
 
-template <int NT, int NK>
+template <int NT, int NP>
 static cudaError_t resident_launch(const Geom& g, const ResidentPlan& p, const ResidentIO& io, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(p.px * p.py);
@@ -1371,7 +1434,7 @@ static cudaError_t resident_launch(const Geom& g, const ResidentPlan& p, const R
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   ResidentShape sh{p.px, p.bx, p.by, p.ex};
-  return cudaLaunchKernelEx(&cfg, step2d_o4_resident<NT, NK>, g, sh, io);
+  return cudaLaunchKernelEx(&cfg, step2d_o4_resident<NT, NP>, g, sh, io);
 }
 
 cudaError_t launch_resident_o4(const Geom& g, const ResidentPlan& p, const ResidentIO& io, cudaStream_t st) {
@@ -1379,9 +1442,9 @@ cudaError_t launch_resident_o4(const Geom& g, const ResidentPlan& p, const Resid
   cudaError_t e = cudaMemsetAsync(io.bar, 0, 2 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   switch (p.shape) {
-    case 0: return resident_launch<RS_SHAPE_THREADS[0], RS_SHAPE_NODES[0]>(g, p, io, st);
-    case 1: return resident_launch<RS_SHAPE_THREADS[1], RS_SHAPE_NODES[1]>(g, p, io, st);
-    case 2: return resident_launch<RS_SHAPE_THREADS[2], RS_SHAPE_NODES[2]>(g, p, io, st);
+    case 0: return resident_launch<RS_SHAPE_THREADS[0], RS_SHAPE_PAIRS[0]>(g, p, io, st);
+    case 1: return resident_launch<RS_SHAPE_THREADS[1], RS_SHAPE_PAIRS[1]>(g, p, io, st);
+    case 2: return resident_launch<RS_SHAPE_THREADS[2], RS_SHAPE_PAIRS[2]>(g, p, io, st);
     default: return cudaErrorInvalidValue;
   }
 }
