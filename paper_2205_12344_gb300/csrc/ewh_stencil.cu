@@ -782,11 +782,13 @@ cudaError_t launch_minvK(const Geom& g, int order, const T* u, T* out, const T* 
 // buffer), recomputes the stresses on block +- 2 from u on block +- 4, forms
 // -D sigma + H^{-1} B sigma and the leapfrog/filter update of its own nodes
 // (same arithmetic as the split kernels), writes its own 4-node rim to the
-// other exchange buffer and meets the other CTAs at a grid barrier: one
-// barrier per level; lambda, mu, 1/(rho h^2) (and f/rho) are the only other
-// global reads.  Barrier waits are bounded in time; on a timeout the kernel raises
-// an error flag, every CTA leaves at its next barrier and fills its
-// accumulator nodes with NaN, which the solve reports as a breakdown.
+// other exchange buffer and counts itself in at a grid barrier; the central
+// stresses of the next level that need no halo are computed before it waits
+// there.  One barrier per level; lambda, mu, 1/(rho h^2) (and f/rho) are the
+// only other global reads.  Barrier waits are bounded in time; on a timeout
+// the kernel raises an error flag, every CTA leaves at its next barrier and
+// fills its accumulator nodes with NaN, which the solve reports as a
+// breakdown.
 // ---------------------------------------------------------------------------
 constexpr int RS_HU = 4;  // u halo
 constexpr int RS_HS = 2;  // stress halo
@@ -803,34 +805,35 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Grid barrier: returns false if it (or another CTA) gave up.  After a
-// __syncthreads that orders the CTA's writes, thread 0 counts the CTA in with
-// a release add and polls with acquire loads; the error flag and the time
-// limit are looked at every 256 polls.
+// Grid barrier pieces: a release add to count a CTA in, acquire loads to
+// poll (see rs_arrive / rs_wait).
 __device__ __forceinline__ void red_release_gpu(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool rs_grid_barrier(unsigned* bar, unsigned target, int* s_ok) {
-  __syncthreads();
+
+// Split form of the grid barrier: rs_arrive after a __syncthreads that
+// orders the CTA's writes (thread 0 counts the CTA in with a release add);
+// rs_wait polls until `target` CTAs have arrived (each wait bounded: it gives
+// up after RS_TIMEOUT_NS or 2^22 polls, or when another CTA raised the error
+// flag, which it then sees every 256 polls) and ends
+// with a __syncthreads.  Work that needs none of the other CTAs' data goes
+// between the two.
+__device__ __forceinline__ void rs_arrive(unsigned* bar) {
+  if (threadIdx.x == 0) red_release_gpu(bar, 1u);
+}
+
+__device__ __forceinline__ bool rs_wait(unsigned* bar, unsigned target, int* s_ok) {
   if (threadIdx.x == 0) {
-    int ok = 1;
-    if (ld_acquire_gpu(bar + 1) != 0u) {
-      ok = 0;
-    } else {
-      red_release_gpu(bar, 1u);
-      const unsigned long long t0 = global_ns();
-      for (unsigned spins = 1; ld_acquire_gpu(bar) < target; ++spins) {
-        if ((spins & 255u) == 0u) {
-          if (ld_acquire_gpu(bar + 1) != 0u) {
-            ok = 0;
-            break;
-          }
-          if (spins > (1u << 22) || global_ns() - t0 > RS_TIMEOUT_NS) {
-            atomicExch(bar + 1, 1u);
-            ok = 0;
-            break;
-          }
+    int ok = ld_acquire_gpu(bar + 1) == 0u;
+    const unsigned long long t0 = global_ns();
+    for (unsigned spins = 1; ok && ld_acquire_gpu(bar) < target; ++spins) {
+      if ((spins & 255u) == 0u) {
+        if (ld_acquire_gpu(bar + 1) != 0u) {
+          ok = 0;
+        } else if (spins > (1u << 22) || global_ns() - t0 > RS_TIMEOUT_NS) {
+          atomicExch(bar + 1, 1u);
+          ok = 0;
         }
       }
     }
@@ -962,6 +965,34 @@ __device__ __forceinline__ void rs_stress_gen(const float* __restrict__ lam, con
   rs_smem[RS_OFF_XY + ps] = m * (u_y + v_x);
 }
 
+// Stresses at the central positions (qx, qy) and (qx + 1, qy), qx even,
+// with 8-byte shared accesses (every plane offset and row stride is even).
+__device__ __forceinline__ void rs_stress_pair(const float* __restrict__ lam, const float* __restrict__ mu, int npx,
+                                               int obase, int qx, int qy) {
+  const int o = obase + (qy - RS_HS) * npx + (qx - RS_HS);
+  const float l0 = __ldg(lam + o), l1 = __ldg(lam + o + 1);
+  const float m0 = __ldg(mu + o), m1 = __ldg(mu + o + 1);
+  const int pu = (qy + RS_HU - RS_HS) * RS_UX + (qx + RS_HU - RS_HS);  // even
+  const float2* U = reinterpret_cast<const float2*>(rs_smem + pu);
+  const float2* V = reinterpret_cast<const float2*>(rs_smem + RS_OFF_V + pu);
+  constexpr int RU = RS_UX / 2;
+  const float2 ua = U[-1], ub = U[0], uc = U[1];
+  const float2 va = V[-1], vb = V[0], vc = V[1];
+  const float ux0 = c4(ua.x, ua.y, ub.y, uc.x), ux1 = c4(ua.y, ub.x, uc.x, uc.y);
+  const float vx0 = c4(va.x, va.y, vb.y, vc.x), vx1 = c4(va.y, vb.x, vc.x, vc.y);
+  const float2 um2 = U[-2 * RU], um1 = U[-RU], up1 = U[RU], up2 = U[2 * RU];
+  const float2 vm2 = V[-2 * RU], vm1 = V[-RU], vp1 = V[RU], vp2 = V[2 * RU];
+  const float uy0 = c4(um2.x, um1.x, up1.x, up2.x), uy1 = c4(um2.y, um1.y, up1.y, up2.y);
+  const float vy0 = c4(vm2.x, vm1.x, vp1.x, vp2.x), vy1 = c4(vm2.y, vm1.y, vp1.y, vp2.y);
+  const float div0 = ux0 + vy0, div1 = ux1 + vy1;
+  const int ps = qy * RS_SX + qx;  // even
+  *reinterpret_cast<float2*>(rs_smem + RS_OFF_XX + ps) =
+      make_float2(l0 * div0 + 2.0f * m0 * ux0, l1 * div1 + 2.0f * m1 * ux1);
+  *reinterpret_cast<float2*>(rs_smem + RS_OFF_YY + ps) =
+      make_float2(l0 * div0 + 2.0f * m0 * vy0, l1 * div1 + 2.0f * m1 * vy1);
+  *reinterpret_cast<float2*>(rs_smem + RS_OFF_XY + ps) = make_float2(m0 * (uy0 + vx0), m1 * (uy1 + vx1));
+}
+
 // Per-level scalars of the leapfrog/filter update.
 struct RsLevel {
   float kt, w0, wnew, cosn;
@@ -1087,6 +1118,17 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
   qb = qa + ((qb - qa) & ~1);  // even width: the rectangle is done in pairs of positions
   if (qb == qa) ra = rb = syn;
   const int wq = qb - qa, nsframe = sxn * syn - wq * (rb - ra);
+  // Of the central positions, those whose stencil reads only the own u (tile
+  // columns and rows [4, w + 4)): [ia, ib) x [ja, jb), even width, computed
+  // while the other CTAs finish the previous level.  In pair columns of the
+  // central rectangle: [pa, pb) x [ja, jb); the rest of the rectangle (the
+  // outer pairs) follows the halo ring.
+  int ia = max(qa, 4), ib = min(qb, wx), ja = max(ra, 4), jb = min(rb, wy);
+  ib = ib > ia ? ia + ((ib - ia) & ~1) : ia;
+  const int wp = wq >> 1;
+  int pa = (ia - qa) >> 1, pb = (ib - qa) >> 1, pja = ja - ra, pjb = jb - ra;
+  if (pb <= pa || pjb <= pja) pa = pb = 0, pja = pjb = rb - ra;
+  const int wpi = pb - pa, nouter = wp * (rb - ra) - wpi * (pjb - pja);
   // Own nodes on central rows and columns: the rectangle [xa, xb) x [ya, yb)
   // of the block (all unknowns, no closure, no boundary term); the others
   // (within 4 nodes of a side of the grid) are the special nodes.
@@ -1121,8 +1163,19 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
   bool alive = true;
   __syncthreads();
 
-  for (int n = 0; n < io.nsteps; ++n) {
-    if (n > 0) {  // halo ring of u^n from the neighbours' rims
+  for (int n = 0;; ++n) {
+    if (wpi > 0) {  // central stresses that need only the own u, in pairs
+      int pp = t % wpi, qy = ja + t / wpi;
+      const int rx = NT % wpi, ry = NT / wpi;
+      for (; qy < jb; walk_next(pp, qy, wpi, rx, ry))
+        rs_stress_pair(io.lam, io.mu, npx, obase, qa + 2 * (pa + pp), qy);
+    }
+    if (n > 0) {
+      if (!rs_wait(io.bar, (unsigned)n * gridDim.x, &s_ok)) {
+        alive = false;
+        break;
+      }
+      // halo ring of u^n from the neighbours' rims
       const float* xbuf = (n & 1) ? io.xbuf1 : io.xbuf0;
       {  // top and bottom strips: tile rows 0..3 and wy+4..wy+7, all columns
         int lx = t % ux, r = t / ux;
@@ -1141,35 +1194,12 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
         su[ly * RS_UX + lx] = __ldcg(xbuf + o);
         sv[ly * RS_UX + lx] = __ldcg(xbuf + F + o);
       }
-      __syncthreads();
     }
-    if (wq > 0) {  // stresses on central positions, two per thread (8-byte shared accesses)
-      const int wp = wq >> 1;
-      int pp = t % wp, qy = ra + t / wp;
-      const int rx = NT % wp, ry = NT / wp;
-      constexpr int RU = RS_UX / 2;
-      for (; qy < rb; walk_next(pp, qy, wp, rx, ry)) {
-        const int qx = qa + 2 * pp;
-        const int o = obase + (qy - RS_HS) * npx + (qx - RS_HS);
-        const float l0 = __ldg(io.lam + o), l1 = __ldg(io.lam + o + 1);
-        const float m0 = __ldg(io.mu + o), m1 = __ldg(io.mu + o + 1);
-        const int pu = (qy + RS_HU - RS_HS) * RS_UX + (qx + RS_HU - RS_HS);  // even
-        const float2* U = reinterpret_cast<const float2*>(su + pu);
-        const float2* V = reinterpret_cast<const float2*>(sv + pu);
-        const float2 ua = U[-1], ub = U[0], uc = U[1];
-        const float2 va = V[-1], vb = V[0], vc = V[1];
-        const float ux0 = c4(ua.x, ua.y, ub.y, uc.x), ux1 = c4(ua.y, ub.x, uc.x, uc.y);
-        const float vx0 = c4(va.x, va.y, vb.y, vc.x), vx1 = c4(va.y, vb.x, vc.x, vc.y);
-        const float2 um2 = U[-2 * RU], um1 = U[-RU], up1 = U[RU], up2 = U[2 * RU];
-        const float2 vm2 = V[-2 * RU], vm1 = V[-RU], vp1 = V[RU], vp2 = V[2 * RU];
-        const float uy0 = c4(um2.x, um1.x, up1.x, up2.x), uy1 = c4(um2.y, um1.y, up1.y, up2.y);
-        const float vy0 = c4(vm2.x, vm1.x, vp1.x, vp2.x), vy1 = c4(vm2.y, vm1.y, vp1.y, vp2.y);
-        const float div0 = ux0 + vy0, div1 = ux1 + vy1;
-        const int ps = qy * RS_SX + qx;  // even
-        *reinterpret_cast<float2*>(sxx + ps) = make_float2(l0 * div0 + 2.0f * m0 * ux0, l1 * div1 + 2.0f * m1 * ux1);
-        *reinterpret_cast<float2*>(syy + ps) = make_float2(l0 * div0 + 2.0f * m0 * vy0, l1 * div1 + 2.0f * m1 * vy1);
-        *reinterpret_cast<float2*>(sxy + ps) = make_float2(m0 * (uy0 + vx0), m1 * (uy1 + vx1));
-      }
+    __syncthreads();
+    for (int j = t; j < nouter; j += NT) {  // the outer central pairs
+      int pc, r;
+      rs_frame_pos(j, wp, rb - ra, pa, pb, pja, pjb, pc, r);
+      rs_stress_pair(io.lam, io.mu, npx, obase, qa + 2 * pc, ra + r);
     }
     for (int j = t; j < nsframe; j += NT) {  // the stress frame: general form
       int qx, qy;
@@ -1276,10 +1306,9 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
         xo[F + o] = sv[pu];
       }
     }
-    if (!L.last && !rs_grid_barrier(io.bar, (unsigned)(n + 1) * gridDim.x, &s_ok)) {
-      alive = false;
-      break;
-    }
+    if (L.last) break;
+    __syncthreads();  // this level's u and rims are written
+    rs_arrive(io.bar);
   }
   // accumulators of the own unknowns (NaN when the barrier gave up)
   const float nanv = __int_as_float(0x7fc00000);
