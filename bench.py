@@ -95,7 +95,7 @@ def kernel_source_hash():
 def step_kernel_name(variant):
     """The 2D order-4 FP32 step kernel behind an autotuner variant number."""
     tiles = {0: "32x8", 1: "32x16", 2: "64x8", 3: "64x4"}
-    shapes = {5: "1024, 7", 6: "768, 9", 7: "512, 14"}
+    shapes = {5: "1024, 4", 6: "768, 5", 7: "512, 7"}
     if variant in tiles:
         return "sbp_stress2d_tl + sbp_div2d_tl (%s tiles), per time level" % tiles[variant]
     if variant == 4:

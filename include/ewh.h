@@ -174,6 +174,18 @@ ewh_status ewh_solve(ewh_ctx* ctx, double tol, int maxit, const double* x0_or_nu
 ewh_status ewh_solve_cr(ewh_ctx* ctx, double tol, int maxit, const double* x0_or_null, double* v_out,
                         ewh_solve_info* info);
 
+/* MINRES on (I - S) v = b in the M inner product (Section 4.4, the remark on
+ * the implicit scheme: when few quadrature points push the discrete filter
+ * transfer function above 1 near a resonance, M(I - S) can be indefinite
+ * and MINRES replaces CG).  Same arguments, layout, ownership and status
+ * codes as ewh_solve; the residual is minimised in the M-norm, so it never
+ * increases.  One S apply per iteration; the recursive residual is replaced
+ * by the FP64 true residual when it reaches tol (FP32 stencil: also each time
+ * it has fallen tenfold), restarting the recurrence from the current iterate.
+ * EWH_EBREAKDOWN if the Lanczos tridiagonal turns singular. */
+ewh_status ewh_solve_minres(ewh_ctx* ctx, double tol, int maxit, const double* x0_or_null, double* v_out,
+                            ewh_solve_info* info);
+
 /* Copy up to cap entries of the last solve's residual history (relative
  * M-norm of the recursive residual after each iteration, max over rhs) to the
  * host array out; returns the number of entries available via *count. */

@@ -20,7 +20,9 @@ What it computes, in the paper's order and notation:
 * Section 3, eq. (el_WHI_OP), with the trapezoidal rule of Section 4 and
   eq. (qoper): Pi u0 = sum_n w_n u^n, w_n = (2/N) eta_n (cos(w t_n) - 1/4);
   S = Pi with f = 0; eq. (many_periods_filter) for K periods.
-* Section 4.5, eq. (amat_sym): CG on M (I - S) v = M Pi 0.
+* Section 4.5, eq. (amat_sym): CG on M (I - S) v = M Pi 0 (conjugate residual as
+  in the Section 4.5 remark; MINRES as in the Section 4.4 remark on indefinite
+  systems).
 * Appendix B: the discrete filter transfer function beta_h.
 
 Parity is pinned by tests/test_oracle_*.py against closed forms, invariants,
@@ -453,6 +455,75 @@ def cr_solve(s: System, tol=1e-8, maxit=10000, x0=None, rhs: int = 0, b=None):
         Ap = Ar + beta * Ap
     info.rel_res = info.history[-1]
     return x, info
+
+
+def minres(apply_A, b, mw, tol=1e-8, maxit=10000, x0=None):
+    """MINRES for a system A x = b whose A is self-adjoint in the inner
+    product (x, y)_W = sum mw x y (Section 4.4, the remark on the implicit
+    scheme: when few quadrature points make beta_h exceed 1 near a resonance
+    the system may be indefinite, and MINRES replaces CG).
+
+    Lanczos in the W inner product builds the tridiagonal T_k; its QR
+    factorisation by Givens rotations gives the iterate minimising the
+    W-norm of the residual over x0 + K_k, updated by the direction recurrence
+    w_k = (v_k - rho2 w_{k-1} - rho3 w_{k-2}) / rho1.  The residual norm is the
+    last rotated right-hand side entry.  Returns x, SolveInfo (history of
+    ||r||_W / ||b||_W)."""
+    def dot(x, y):
+        return float(np.dot(mw * x, y))
+
+    bb = math.sqrt(dot(b, b))
+    info = SolveInfo()
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    r = b - apply_A(x) if x0 is not None else b.copy()
+    beta = math.sqrt(dot(r, r))
+    info.history.append(beta / bb)
+    if info.history[-1] <= tol:
+        info.converged, info.rel_res = True, info.history[-1]
+        return x, info
+    v_prev = np.zeros_like(b)
+    v = r / beta
+    w1 = np.zeros_like(b)   # w_{k-1}
+    w2 = np.zeros_like(b)   # w_{k-2}
+    c1, s1 = 1.0, 0.0       # rotation k-1
+    c2, s2 = 1.0, 0.0       # rotation k-2
+    eta = beta
+    for it in range(1, maxit + 1):
+        # Lanczos step: A v_k = beta_k v_{k-1} + alpha_k v_k + beta_{k+1} v_{k+1}
+        z = apply_A(v) - beta * v_prev
+        alpha = dot(v, z)
+        z = z - alpha * v
+        beta_next = math.sqrt(max(dot(z, z), 0.0))
+        # the previous two rotations act on the new column (0, beta_k, alpha_k, beta_{k+1})
+        rho3 = s2 * beta
+        t = c2 * beta
+        rho2 = c1 * t + s1 * alpha
+        delta = -s1 * t + c1 * alpha
+        rho1 = math.hypot(delta, beta_next)
+        if rho1 == 0.0:
+            raise ZeroDivisionError("MINRES: singular tridiagonal")
+        c, sn = delta / rho1, beta_next / rho1
+        w = (v - rho2 * w1 - rho3 * w2) / rho1
+        x = x + (c * eta) * w
+        eta = -sn * eta
+        info.history.append(abs(eta) / bb)
+        info.iters = it
+        if info.history[-1] <= tol or beta_next == 0.0:
+            info.converged = info.history[-1] <= tol or beta_next == 0.0
+            break
+        w2, w1 = w1, w
+        c2, s2, c1, s1 = c1, s1, c, sn
+        v_prev, v = v, z / beta_next
+        beta = beta_next
+    info.rel_res = info.history[-1]
+    return x, info
+
+
+def minres_solve(s: System, tol=1e-8, maxit=10000, x0=None, rhs: int = 0, b=None):
+    """MINRES on (I - S) v = b in the M inner product (one S apply per iteration)."""
+    if b is None:
+        b = apply_Pi0(s, rhs)
+    return minres(lambda v: v - apply_S(s, v, rhs), b, s.Mdiag, tol=tol, maxit=maxit, x0=x0)
 
 
 def helmholtz_direct(s: System, rhs: int = 0):

@@ -60,6 +60,7 @@ SIGNATURES = {
     "ewh_mdot": (ctypes.c_int, [_P, _P, _P, _D]),
     "ewh_solve": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, _P, _P, ctypes.POINTER(ewh_solve_info)]),
     "ewh_solve_cr": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, _P, _P, ctypes.POINTER(ewh_solve_info)]),
+    "ewh_solve_minres": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, _P, _P, ctypes.POINTER(ewh_solve_info)]),
     "ewh_residual_history": (ctypes.c_int, [_P, _D, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "ewh_kernel_launches": (ctypes.c_longlong, [_P]),
     "ewh_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ewh_stats)]),
@@ -194,6 +195,14 @@ def ewh_solve(ctx, tol, maxit, x0, v_out, raise_on_error=True):
 def ewh_solve_cr(ctx, tol, maxit, x0, v_out, raise_on_error=True):
     info = ewh_solve_info()
     s = load().ewh_solve_cr(ctx, float(tol), int(maxit), _ptr(x0), _ptr(v_out), ctypes.byref(info))
+    if raise_on_error and s not in (EWH_OK,):
+        _check(s, ctx)
+    return info
+
+
+def ewh_solve_minres(ctx, tol, maxit, x0, v_out, raise_on_error=True):
+    info = ewh_solve_info()
+    s = load().ewh_solve_minres(ctx, float(tol), int(maxit), _ptr(x0), _ptr(v_out), ctypes.byref(info))
     if raise_on_error and s not in (EWH_OK,):
         _check(s, ctx)
     return info

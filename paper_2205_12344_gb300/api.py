@@ -93,6 +93,14 @@ class WaveHoltz:
         info = L.ewh_solve_cr(self.ctx, tol, maxit, x0v, out, raise_on_error=raise_on_error)
         return out, info
 
+    def solve_minres(self, tol=1e-8, maxit=100000, x0=None, raise_on_error=True):
+        """MINRES instead of CG: for systems that may be indefinite (few time
+        steps per period near a resonance); the residual never increases."""
+        out = self._vec()
+        x0v = self._vec(x0) if x0 is not None else None
+        info = L.ewh_solve_minres(self.ctx, tol, maxit, x0v, out, raise_on_error=raise_on_error)
+        return out, info
+
     def residual_history(self):
         return L.ewh_residual_history(self.ctx)
 

@@ -926,6 +926,155 @@ ewh_status run_cr(ewh_ctx* ctx, double* x, double* r, double tol, int maxit, dou
   return EWH_OK;
 }
 
+// MINRES in the M inner product (Section 4.4, the remark on the implicit
+// scheme: with few quadrature points near a resonance the discrete filter
+// transfer function can exceed 1 and M(I - S) become indefinite; MINRES then
+// replaces CG).  Lanczos in the M inner product builds T_k; Givens rotations
+// factor it, and the iterate minimising ||b - A x||_M over x0 + K_k follows
+// from the direction recurrence w_k = (v_k - rho2 w_{k-1} - rho3 w_{k-2})/rho1.
+// One S apply (precision T) per iteration; the right-hand sides advance
+// together, each with its own Lanczos and rotation scalars (host, FP64).  When
+// the recursive residual |eta| reaches tol (or, for FP32, falls by `drop`
+// since the last check, or the Krylov space is exhausted) the FP64 true
+// residual replaces it and the recurrence restarts from the current iterate;
+// convergence is declared on the true residual only.
+template <typename T>
+ewh_status run_minres(ewh_ctx* ctx, double* x, double* r, double tol, int maxit, double drop, ewh_solve_info* inf,
+                      double* rel_out) {
+  const Geom& g = ctx->g;
+  const int R = g.nrhs;
+  const long long n = total_unknowns(ctx);
+  const long long seg = n / R;  // unknowns of one right-hand side
+  ewh_status st = ensure_graph<T>(ctx, false);
+  if (st != EWH_OK) return st;
+  double* v_prev = ctx->kp;
+  double* v = ctx->kq;
+  double* z = ctx->kar;
+  double* w1 = ctx->kap;  // w_{k-1}
+  double* w2 = ctx->kd;   // w_{k-2}, overwritten by w_k
+  std::vector<double> bnorm(R), beta(R), eta(R), c1(R), s1(R), c2(R), s2(R), true_res(R), anchor(R), alpha(R),
+      beta_next(R);
+  std::vector<char> act(R, 0);
+  auto fetch = [&](int which, std::vector<double>& out) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * S_N * R, cudaMemcpyDeviceToHost, ctx->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    for (int k = 0; k < R; ++k) out[k] = ctx->h_scal[which * R + k];
+    return e;
+  };
+  {
+    std::vector<double> bb(R);
+    EWH_CU(fetch(S_BB, bb));
+    for (int k = 0; k < R; ++k) bnorm[k] = std::sqrt(bb[k]);
+  }
+  // (re)start from the true residual r of x: v = r / ||r||_M
+  auto restart = [&](bool first) -> ewh_status {
+    ewh_status e2 = mdot_dev(ctx, r, r, sc(ctx, S_DOT));
+    if (e2 != EWH_OK) return e2;
+    std::vector<double> rr(R);
+    EWH_CU(fetch(S_DOT, rr));
+    EWH_CU(cudaMemsetAsync(v, 0, sizeof(double) * n, ctx->st));
+    EWH_CU(cudaMemsetAsync(v_prev, 0, sizeof(double) * n, ctx->st));
+    EWH_CU(cudaMemsetAsync(w1, 0, sizeof(double) * n, ctx->st));
+    EWH_CU(cudaMemsetAsync(w2, 0, sizeof(double) * n, ctx->st));
+    for (int k = 0; k < R; ++k) {
+      beta[k] = std::sqrt(rr[k]);
+      true_res[k] = anchor[k] = beta[k] / bnorm[k];
+      if (first) act[k] = true_res[k] > tol;
+      else act[k] = act[k] && true_res[k] > tol;
+      c1[k] = c2[k] = 1.0;
+      s1[k] = s2[k] = 0.0;
+      eta[k] = beta[k];
+      if (act[k]) {
+        EWH_CU(launch_axpby(seg, 1.0 / beta[k], r + k * seg, 1.0, v + k * seg, ctx->st));
+        ctx->launches += 1;
+      }
+    }
+    return EWH_OK;
+  };
+  auto worst = [&]() {
+    double m = 0.0;
+    for (double t : true_res) m = std::max(m, t);
+    return m;
+  };
+  st = restart(true);
+  if (st != EWH_OK) return st;
+  ctx->history.push_back(worst());
+  auto any_active = [&]() {
+    for (char a : act)
+      if (a) return true;
+    return false;
+  };
+  while (any_active() && inf->iters < maxit) {
+    // Lanczos: z = A v - beta_k v_{k-1}; alpha = (v, z)_M; z -= alpha v; beta_{k+1} = ||z||_M
+    st = ar_apply<T>(ctx, v, z);
+    if (st != EWH_OK) return st;
+    for (int k = 0; k < R; ++k)
+      if (act[k]) EWH_CU(launch_axpby(seg, -beta[k], v_prev + k * seg, 1.0, z + k * seg, ctx->st));
+    st = mdot_dev(ctx, v, z, sc(ctx, S_DOT));
+    if (st != EWH_OK) return st;
+    EWH_CU(fetch(S_DOT, alpha));
+    for (int k = 0; k < R; ++k)
+      if (act[k]) EWH_CU(launch_axpby(seg, -alpha[k], v + k * seg, 1.0, z + k * seg, ctx->st));
+    st = mdot_dev(ctx, z, z, sc(ctx, S_DOT));
+    if (st != EWH_OK) return st;
+    EWH_CU(fetch(S_DOT, beta_next));
+    ++inf->iters;
+    if (sizeof(T) == 8) ++inf->s_applies_fp64;
+    else ++inf->s_applies;
+    bool check = false;
+    double hist = 0.0;
+    for (int k = 0; k < R; ++k) {
+      if (!act[k]) continue;
+      const double bn = std::sqrt(std::max(beta_next[k], 0.0));
+      // the two previous rotations act on the new column (0, beta_k, alpha_k, beta_{k+1})
+      const double rho3 = s2[k] * beta[k];
+      const double tt = c2[k] * beta[k];
+      const double rho2 = c1[k] * tt + s1[k] * alpha[k];
+      const double delta = -s1[k] * tt + c1[k] * alpha[k];
+      const double rho1 = std::hypot(delta, bn);
+      if (!(rho1 > 0.0) || !std::isfinite(rho1)) {
+        *rel_out = worst();
+        return fail(ctx, EWH_EBREAKDOWN, "MINRES breakdown: singular or non-finite tridiagonal");
+      }
+      const double c = delta / rho1, sn = bn / rho1;
+      // w_k = (v_k - rho2 w_{k-1} - rho3 w_{k-2}) / rho1 (into the w_{k-2} buffer); x += c eta w_k
+      EWH_CU(launch_axpby(seg, -rho2 / rho1, w1 + k * seg, -rho3 / rho1, w2 + k * seg, ctx->st));
+      EWH_CU(launch_axpby(seg, 1.0 / rho1, v + k * seg, 1.0, w2 + k * seg, ctx->st));
+      EWH_CU(launch_axpby(seg, c * eta[k], w2 + k * seg, 1.0, x + k * seg, ctx->st));
+      // v_{k+1} = z / beta_{k+1} (in place in z)
+      if (bn > 0.0) EWH_CU(launch_axpby(seg, 0.0, z + k * seg, 1.0 / bn, z + k * seg, ctx->st));
+      ctx->launches += 6;
+      eta[k] = -sn * eta[k];
+      c2[k] = c1[k];
+      s2[k] = s1[k];
+      c1[k] = c;
+      s1[k] = sn;
+      beta[k] = bn;
+      const double res = std::fabs(eta[k]) / bnorm[k];
+      hist = std::max(hist, res);
+      if (res <= tol || (drop > 0.0 && res <= drop * anchor[k]) || bn == 0.0) check = true;
+    }
+    ctx->launches += 4;
+    ctx->history.push_back(hist);
+    // rotate buffers: (v_prev, v, z) <- (v, z, v_prev); (w1, w2) <- (w_k, w_{k-1})
+    std::swap(w1, w2);
+    double* tmp = v_prev;
+    v_prev = v;
+    v = z;
+    z = tmp;
+    if (check) {
+      double dummy = 0.0;
+      st = true_residual(ctx, x, r, &dummy);
+      if (st != EWH_OK) return st;
+      ++inf->s_applies_fp64;
+      st = restart(false);
+      if (st != EWH_OK) return st;
+    }
+  }
+  *rel_out = worst();
+  return EWH_OK;
+}
+
 ewh_status solve_impl(ewh_ctx* ctx, double tol, int maxit, const double* x0, double* v_out,
                       ewh_solve_info* inf, int method = 0) {
   const Geom& g = ctx->g;
@@ -953,7 +1102,10 @@ ewh_status solve_impl(ewh_ctx* ctx, double tol, int maxit, const double* x0, dou
   // every time the recursive residual fell tenfold, so the FP32 operator's
   // rounding never accumulates in the residual beyond one decade.
   ewh_status result;
-  if (method == 1) {
+  if (method == 2) {
+    result = ctx->precision == EWH_FP64 ? run_minres<double>(ctx, ctx->kx, ctx->kr, tol, maxit, 0.0, inf, &rel)
+                                        : run_minres<float>(ctx, ctx->kx, ctx->kr, tol, maxit, 0.1, inf, &rel);
+  } else if (method == 1) {
     result = ctx->precision == EWH_FP64 ? run_cr<double>(ctx, ctx->kx, ctx->kr, tol, maxit, 0.0, inf, &rel)
                                         : run_cr<float>(ctx, ctx->kx, ctx->kr, tol, maxit, 0.1, inf, &rel);
   } else if (ctx->precision == EWH_FP64) {
@@ -1507,6 +1659,26 @@ ewh_status ewh_solve_cr(ewh_ctx* ctx, double tol, int maxit, const double* x0_or
   enter(ctx);
   ewh_solve_info inf{};
   s = solve_impl(ctx, tol, maxit, x0_or_null, v_out, &inf, 1);
+  leave(ctx);
+  cudaStreamSynchronize(ctx->st);
+  inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  inf.status = s;
+  if (info) *info = inf;
+  if (s == EWH_OK) s = check_async(ctx);
+  return s;
+}
+
+ewh_status ewh_solve_minres(ewh_ctx* ctx, double tol, int maxit, const double* x0_or_null, double* v_out,
+                            ewh_solve_info* info) {
+  if (!ctx || !v_out) return fail(ctx, EWH_EINVAL, "null argument");
+  if (!(tol > 0.0) || maxit < 0) return fail(ctx, EWH_EINVAL, "tol must be > 0 and maxit >= 0");
+  if (!ctx->has_forcing) return fail(ctx, EWH_EINVAL, "problem was created without forcing");
+  ewh_status s = check_async(ctx);
+  if (s != EWH_OK) return s;
+  const auto t0 = std::chrono::steady_clock::now();
+  enter(ctx);
+  ewh_solve_info inf{};
+  s = solve_impl(ctx, tol, maxit, x0_or_null, v_out, &inf, 2);
   leave(ctx);
   cudaStreamSynchronize(ctx->st);
   inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -299,3 +299,41 @@ def test_conjugate_residual_matches_oracle():
     with _wh(p, "fp32") as wh:
         x32, i32 = wh.solve_cr(tol=1e-8)
     assert i32.status == 0 and i32.rel_res <= 1e-8
+
+
+def test_minres_matches_oracle():
+    """ewh_solve_minres (FP64) follows the oracle's MINRES residual history and
+    reaches the direct solution; the FP32-stencil variant meets the FP64
+    residual tolerance (Section 4.4 remark)."""
+    p = inputs.cfg_homogeneous_2d(nu=32, omega=10.0)
+    s = O.build_system(p)
+    xo, io = O.minres_solve(s, tol=1e-9)
+    v = O.helmholtz_direct(s)
+    with _wh(p) as wh:
+        x, info = wh.solve_minres(tol=1e-9)
+        hist = wh.residual_history()
+    assert info.status == 0 and abs(info.iters - io.iters) <= 1
+    n = min(15, len(hist), len(io.history))
+    assert np.allclose(hist[:n], io.history[:n], rtol=1e-7, atol=0)
+    assert np.all(np.diff(hist[:n]) <= 1e-12)
+    assert np.linalg.norm(to_np(x) - v) <= 1e-6 * np.linalg.norm(v)
+    with _wh(p, "fp32") as wh:
+        x32, i32 = wh.solve_minres(tol=1e-8)
+    assert i32.status == 0 and i32.rel_res <= 1e-8
+    assert rel_err(to_np(x32), v) < 1e-5
+
+
+def test_minres_solves_indefinite_system():
+    """N_t = 5 near a resonance: M(I - S) is indefinite (the oracle test pins
+    that with the dense S) yet the stable scheme's fixed point is the discrete
+    Helmholtz solution.  GPU MINRES reaches it with a non-increasing residual."""
+    p = inputs.small_problem(2, [6, 5], 2, [0, 1, 0, 0], seed=3, omega=24.75)
+    s = O.build_system(p, nt=5)
+    v = O.helmholtz_direct(s)
+    with _wh(p, nt=5) as wh:
+        assert wh.info.nt == 5
+        x, info = wh.solve_minres(tol=1e-11, maxit=500)
+        hist = wh.residual_history()
+    assert info.status == 0 and info.rel_res <= 1e-11
+    assert np.all(np.diff(hist) <= 1e-12)
+    assert np.linalg.norm(to_np(x) - v) <= 1e-8 * np.linalg.norm(v)

@@ -516,3 +516,69 @@ def test_conjugate_residual_converges_monotonically():
     assert np.linalg.norm(x - v) <= 1e-8 * np.linalg.norm(v)
     h = np.array(info.history)
     assert np.all(np.diff(h) <= 1e-12 * h[0])
+
+
+def _w_selfadjoint_indefinite(n, n_neg, seed):
+    """A matrix self-adjoint in the W inner product with n_neg negative and
+    n - n_neg positive eigenvalues: W^{-1/2} Q diag(l) Q^T W^{1/2}."""
+    rng = np.random.default_rng(seed)
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.concatenate([rng.uniform(-2.0, -0.3, n_neg), rng.uniform(0.2, 3.0, n - n_neg)])
+    mw = rng.uniform(0.5, 2.0, n)
+    wh = np.sqrt(mw)
+    a = ((q * lam) @ q.T) * wh[None, :] / wh[:, None]
+    return a, mw, rng.standard_normal(n)
+
+
+@pytest.mark.parametrize("n_neg", [0, 7, 20])
+def test_minres_solves_w_selfadjoint_systems(n_neg):
+    """Section 4.4 remark (MINRES for indefinite systems): on W-self-adjoint
+    systems, definite or not, the oracle's MINRES reaches numpy's solution,
+    terminates within n + 5 iterations (finite termination of the Krylov
+    method) and its W-norm residual never increases.  Its reported residual
+    is the true one."""
+    n = 30
+    a, mw, b = _w_selfadjoint_indefinite(n, n_neg, 7 + n_neg)
+    x, info = O.minres(lambda v: a @ v, b, mw, tol=1e-12, maxit=200)
+    want = np.linalg.solve(a, b)
+    assert info.converged and info.iters <= n + 5
+    assert np.linalg.norm(x - want) <= 1e-9 * np.linalg.norm(want)
+    h = np.array(info.history)
+    assert np.all(np.diff(h) <= 1e-14)
+    r = b - a @ x
+    true = math.sqrt(np.dot(mw * r, r) / np.dot(mw * b, b))
+    assert abs(true - info.rel_res) <= 1e-10
+
+
+def test_minres_solves_indefinite_wave_holtz_system():
+    """Few time steps per period (N_t = 5) near a resonance make the discrete
+    filter exceed 1 on one mode (Appendix B), so M(I - S) is indefinite while
+    the scheme is stable: checked here with the dense S.  MINRES still
+    reaches the discrete Helmholtz solution, monotonically."""
+    p = inputs.small_problem(2, [6, 5], 2, [0, 1, 0, 0], seed=3, omega=24.75)
+    s = O.build_system(p, nt=5)
+    S = O.form_S(s)
+    mh = np.sqrt(s.Mdiag)
+    a_sym = ((np.eye(S.shape[0]) - S) * mh[:, None]) / mh[None, :]
+    ev = np.linalg.eigvalsh(0.5 * (a_sym + a_sym.T))
+    assert ev.min() < -1e-3 and ev.max() < 1.5          # indefinite, and stable
+    v = O.helmholtz_direct(s)
+    x, info = O.minres_solve(s, tol=1e-11, maxit=500)
+    assert info.converged
+    assert np.linalg.norm(x - v) <= 1e-8 * np.linalg.norm(v)
+    h = np.array(info.history)
+    assert np.all(np.diff(h) <= 1e-14)
+
+
+def test_minres_on_definite_system_matches_conjugate_residual():
+    """On the SPD system M(I - S) of the explicit scheme, MINRES and CR both
+    minimise the M-norm residual over the same Krylov spaces, so their
+    residual histories agree (to rounding) and both reach the direct solution."""
+    s = O.build_system(_case(2, 4, [0, 0, 0, 1], 1, seed=3))
+    v = O.helmholtz_direct(s)
+    xm, im = O.minres_solve(s, tol=1e-10, maxit=500)
+    xc, ic = O.cr_solve(s, tol=1e-10, maxit=500)
+    assert im.converged and ic.converged
+    n = min(20, len(im.history), len(ic.history))
+    assert np.allclose(im.history[:n], ic.history[:n], rtol=1e-6, atol=1e-13)
+    assert np.linalg.norm(xm - v) <= 1e-7 * np.linalg.norm(v)
