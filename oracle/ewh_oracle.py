@@ -23,6 +23,7 @@ What it computes, in the paper's order and notation:
 * Section 4.5, eq. (amat_sym): CG on M (I - S) v = M Pi 0 (conjugate residual as
   in the Section 4.5 remark; MINRES as in the Section 4.4 remark on indefinite
   systems).
+* Section 4.4: the implicit (corrected) scheme, each level a sparse solve.
 * Appendix B: the discrete filter transfer function beta_h.
 
 Parity is pinned by tests/test_oracle_*.py against closed forms, invariants,
@@ -145,6 +146,9 @@ class System:
     omega_tilde: float = 0.0
     weights: np.ndarray = None       # trapezoid filter weights, length periods*nt+1
     corrected: int = 1
+    implicit: int = 0                # 1: the implicit scheme of Section 4.4
+    alpha: float = 2.0               # its centre coefficient (eq. alpha; 2 when uncorrected)
+    impl_lu: object = None           # factorisation of M + (dt^2/2) K (implicit scheme)
 
 
 def sbp4_first_derivative(N):
@@ -303,6 +307,14 @@ def build_system(prob, nt: Optional[int] = None) -> System:
     s.c = (s.omega_tilde / prob.omega) ** 2 if prob.corrected else 1.0
     s.kt = s.c * s.dt ** 2
     s.weights = filter_weights(nt, prob.periods)
+    if getattr(prob, "implicit", 0):
+        # Section 4.4: (u^{n+1} - alpha u^n + u^{n-1}) / dt^2 = (1/2) L_h (u^{n+1} + u^{n-1})
+        #              - f cos(w t_n) cos(w dt),  alpha = cos(w dt) (2 + w^2 dt^2) (eq. alpha)
+        s.implicit = 1
+        wd = prob.omega * s.dt
+        s.alpha = math.cos(wd) * (2.0 + wd * wd) if prob.corrected else 2.0
+        s.omega_tilde = 2.0 * math.sin(wd / 2.0) / (s.dt * math.sqrt(math.cos(wd))) if math.cos(wd) > 0 else float("nan")
+        s.kt = 0.0
     return s
 
 
@@ -315,9 +327,43 @@ def minv_K(s: System, u):
     return (s.K @ u) / s.Mdiag
 
 
+def apply_Pi_implicit(s: System, u0, rhs: int = 0, forced: bool = True):
+    """Pi u0 / S u0 with the implicit scheme of Section 4.4, in the mass form
+    (M + (dt^2/2) K) u^{n+1} = alpha M u^n - (M + (dt^2/2) K) u^{n-1}
+                                - dt^2 W f cos(w t_n) cos(w dt),
+    started from (M + (dt^2/2) K) u^{-1} = (alpha/2) M u0 - (dt^2/2) W f cos(w dt)
+    (the paper's modified initial data), with the trapezoidal filter
+    accumulation of eq. (qoper).  Each level is a sparse direct solve."""
+    dt = s.dt
+    c = 0.5 * dt * dt
+    if s.impl_lu is None:
+        s.impl_lu = spla.splu((sp.diags(s.Mdiag) + c * s.K).tocsc())
+    lu = s.impl_lu
+    cdt = math.cos(s.omega * dt)
+    wf = s.Wdiag * s.f_u[rhs] if forced else np.zeros_like(u0)
+
+    def B(u):
+        return s.Mdiag * u + c * (s.K @ u)
+
+    u_prev = lu.solve(s.Mdiag * (0.5 * s.alpha * u0) - c * wf * cdt)
+    u = u0.copy()
+    acc = s.weights[0] * u
+    N = s.nt * s.periods
+    for n in range(N):
+        cos_n = math.cos(2.0 * math.pi * n / s.nt)
+        u_next = lu.solve(s.alpha * (s.Mdiag * u) - B(u_prev) - dt * dt * wf * cos_n * cdt)
+        u_prev, u = u, u_next
+        acc = acc + s.weights[n + 1] * u
+    return acc
+
+
 def apply_Pi(s: System, u0, rhs: int = 0, forced: bool = True, return_history=False):
     """Pi u0 (forced) or S u0 (forced=False): corrected leapfrog over
-    periods*nt steps with the trapezoidal filter accumulation."""
+    periods*nt steps with the trapezoidal filter accumulation (the implicit
+    scheme when the system was built with it)."""
+    if s.implicit:
+        assert not return_history
+        return apply_Pi_implicit(s, u0, rhs, forced)
     kt = s.kt
     N = s.nt * s.periods
     g = s.f_over_rho[rhs] if forced else np.zeros_like(u0)

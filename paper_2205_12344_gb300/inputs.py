@@ -47,6 +47,7 @@ class Problem:
     cfl: float = 0.5
     periods: int = 1
     corrected: int = 1
+    implicit: int = 0       # 1: implicit time stepping (needs an explicit nt >= 5)
 
     @property
     def nrhs(self) -> int:

@@ -582,3 +582,72 @@ def test_minres_on_definite_system_matches_conjugate_residual():
     n = min(20, len(im.history), len(ic.history))
     assert np.allclose(im.history[:n], ic.history[:n], rtol=1e-6, atol=1e-13)
     assert np.linalg.norm(xm - v) <= 1e-7 * np.linalg.norm(v)
+
+
+# ---------------------------------------------------------------- implicit scheme (Section 4.4)
+
+IMPLICIT_CASES = [(2, 2, [0, 0, 0, 1], 5), (2, 4, [1, 0, 0, 1], 12), (3, 2, [0, 0, 0, 0, 0, 1], 7)]
+
+
+def _implicit(dim, order, bc, corrected=1, seed=7):
+    p = _case(dim, order, bc, 1, seed=seed)
+    p.implicit = 1
+    p.corrected = corrected
+    return p
+
+
+@pytest.mark.parametrize("dim,order,bc,nt", IMPLICIT_CASES)
+@pytest.mark.parametrize("corrected", [1, 0])
+def test_implicit_fixed_point(dim, order, bc, nt, corrected):
+    """Section 4.4: with alpha = cos(w dt)(2 + w^2 dt^2) and the modified start,
+    the solution of (w^2 M - K) v = W f is an exact fixed point of Pi_h; the
+    unmodified scheme (alpha = 2) converges to the Helmholtz solution at the
+    shifted frequency w~ = 2 sin(w dt / 2) / (dt sqrt(cos(w dt)))."""
+    s = O.build_system(_implicit(dim, order, bc, corrected), nt=nt)
+    wd = s.omega * s.dt
+    if corrected:
+        assert abs(s.alpha - math.cos(wd) * (2 + wd * wd)) < 1e-15
+        w_eff = s.omega
+    else:
+        assert s.alpha == 2.0
+        w_eff = 2.0 * math.sin(wd / 2.0) / (s.dt * math.sqrt(math.cos(wd)))
+    A = (w_eff * w_eff) * np.diag(s.Mdiag) - s.K.toarray()
+    v = np.linalg.solve(A, s.Wdiag * s.f_u[0])
+    assert np.linalg.norm(O.apply_Pi(s, v) - v) <= 1e-11 * np.linalg.norm(v)
+
+
+@pytest.mark.parametrize("dim,order,bc,nt", IMPLICIT_CASES[:2])
+def test_implicit_S_self_adjoint_and_eigenvalues(dim, order, bc, nt):
+    """M (I - S) is symmetric for the implicit scheme too, and S acts on each
+    eigenmode of M^{-1} K (eigenvalue k2) by sum_n w_n cos(n theta) with
+    cos theta = alpha / (2 + dt^2 k2) (the mode recurrence of the scheme)."""
+    s = O.build_system(_implicit(dim, order, bc), nt=nt)
+    S = O.form_S(s)
+    A = np.diag(s.Mdiag) @ (np.eye(S.shape[0]) - S)
+    assert np.abs(A - A.T).max() <= 1e-12 * np.abs(A).max()
+    ms = np.sqrt(s.Mdiag)
+    kap = np.linalg.eigvalsh(s.K.toarray() / ms[:, None] / ms[None, :])
+    theta = np.arccos(s.alpha / (2.0 + s.dt ** 2 * kap))
+    pred = np.sort(np.cos(np.outer(theta, np.arange(len(s.weights)))) @ s.weights)
+    got = np.sort(np.linalg.eigvals(S).real)
+    assert np.abs(pred - got).max() < 1e-11
+
+
+def test_implicit_alpha_stability_bound():
+    """Section 4.4: stability needs |alpha| < 2; alpha = cos(2 pi / k)(2 + (2 pi / k)^2)
+    meets it for every k >= 5 time steps per period and fails at k = 3."""
+    for k in range(5, 400):
+        a = math.cos(2 * math.pi / k) * (2 + (2 * math.pi / k) ** 2)
+        assert abs(a) < 2.0
+    a3 = math.cos(2 * math.pi / 3) * (2 + (2 * math.pi / 3) ** 2)
+    assert abs(a3) > 2.0
+
+
+def test_implicit_krylov_solves():
+    """CG and MINRES on the implicit scheme's system reach the direct solution."""
+    s = O.build_system(_implicit(2, 2, [0, 0, 0, 1]), nt=8)
+    v = O.helmholtz_direct(s)
+    x, info = O.cg_solve(s, tol=1e-11, maxit=500)
+    assert info.converged and np.linalg.norm(x - v) <= 1e-9 * np.linalg.norm(v)
+    xm, im = O.minres_solve(s, tol=1e-11, maxit=500)
+    assert im.converged and np.linalg.norm(xm - v) <= 1e-9 * np.linalg.norm(v)
