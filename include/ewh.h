@@ -82,6 +82,15 @@ typedef struct {
   int corrected;  /* 1: time-corrected scheme (Section 4.3, default);
                      0: standard leapfrog (converges to the w~ problem) */
   int nt;         /* time steps per period; 0 = ceil(T / dt_CFL), at least 5 */
+  int implicit;   /* 0: explicit leapfrog (above).  1: the implicit scheme of
+                     Section 4.4 (eq. ImplicitScheme; with corrected = 1 the
+                     modified alpha = cos(w dt)(2 + w^2 dt^2) and start, so
+                     the fixed point is the w problem; with 0, the w~ =
+                     2 sin(w dt/2)/(dt sqrt(cos w dt)) problem).  Needs
+                     precision EWH_FP64 and an explicit nt >= 5 (no CFL
+                     limit); each level solves with I + (dt^2/2) M^{-1} K by
+                     CG in the M inner product on the device.  Not for
+                     batches. */
 } ewh_grid_desc;
 
 /* Scalars of a created problem. */

@@ -19,7 +19,7 @@ class ewh_grid_desc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("h", ctypes.c_double),
                 ("order", ctypes.c_int), ("bc", ctypes.c_int * 6), ("precision", ctypes.c_int),
                 ("cfl", ctypes.c_double), ("periods", ctypes.c_int), ("corrected", ctypes.c_int),
-                ("nt", ctypes.c_int)]
+                ("nt", ctypes.c_int), ("implicit", ctypes.c_int)]
 
 
 class ewh_problem_info(ctypes.Structure):

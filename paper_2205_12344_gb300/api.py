@@ -8,7 +8,7 @@ import numpy as np
 from . import _lib as L
 
 
-def make_desc(dim, n, h, order, bc, precision=L.EWH_FP64, cfl=0.5, periods=1, corrected=1, nt=0):
+def make_desc(dim, n, h, order, bc, precision=L.EWH_FP64, cfl=0.5, periods=1, corrected=1, nt=0, implicit=0):
     d = L.ewh_grid_desc()
     d.dim = int(dim)
     for a in range(3):
@@ -23,6 +23,7 @@ def make_desc(dim, n, h, order, bc, precision=L.EWH_FP64, cfl=0.5, periods=1, co
     d.periods = int(periods)
     d.corrected = int(corrected)
     d.nt = int(nt)
+    d.implicit = int(implicit)
     return d
 
 
@@ -40,7 +41,7 @@ class WaveHoltz:
         self.prob = prob
         self.precision = precision
         desc = make_desc(prob.dim, prob.n, prob.h, prob.order, prob.bc, PRECISIONS[precision],
-                         prob.cfl, prob.periods, prob.corrected, nt)
+                         prob.cfl, prob.periods, prob.corrected, nt, getattr(prob, "implicit", 0))
         rho = np.ascontiguousarray(prob.rho, dtype=np.float64)
         lam = np.ascontiguousarray(prob.lam, dtype=np.float64)
         mu = np.ascontiguousarray(prob.mu, dtype=np.float64)
@@ -146,7 +147,7 @@ class WaveHoltzBatch:
         items = []
         for p in self.probs:
             desc = make_desc(p.dim, p.n, p.h, p.order, p.bc, PRECISIONS[precision], p.cfl, p.periods,
-                             p.corrected, 0)
+                             p.corrected, 0, getattr(p, "implicit", 0))
             arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (p.rho, p.lam, p.mu, p.forcing)]
             self._keep.append(arrs)
             items.append((desc, arrs[0], arrs[1], arrs[2], p.omega, arrs[3], p.nrhs))

@@ -87,6 +87,13 @@ struct ewh_ctx {
   int nblk = 1;
   long long launches = 0;
   bool allow_resident = true;  // false for batch members (their branches run concurrently)
+  // implicit scheme (Section 4.4; FP64, dense unknown layout): level vectors,
+  // inner-solve vectors, f/rho, device scalars of the inner CG
+  int implicit = 0;
+  double alpha = 2.0;
+  double *iu_prev = nullptr, *iu = nullptr, *iu_next = nullptr, *ig = nullptr, *ir = nullptr, *ip = nullptr,
+         *iq = nullptr, *iacc = nullptr, *ifr = nullptr, *iscal = nullptr;
+  long long inner_iters = 0;  // inner CG iterations of the implicit levels (accounting)
   std::string err = "no error";
   std::vector<double> history;
   // device timing of wave solves: pending event pairs, reusable events
@@ -589,8 +596,153 @@ ewh_status run_wave(ewh_ctx* ctx, const double* v_in, bool forced) {
   return EWH_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Implicit scheme (Section 4.4, eq. ImplicitScheme with the modified alpha
+// and start), in mass form with B = I + (dt^2/2) M^{-1} K:
+//   B u^{-1}  = (alpha/2) u^0 - (dt^2/2) (f/rho) cos(w dt),
+//   B u^{n+1} = alpha u^n - B u^{n-1} - dt^2 (f/rho) cos(w t_n) cos(w dt),
+// accumulated by the trapezoidal filter.  Each level solves with B by CG in
+// the M inner product (B is M-self-adjoint and positive definite), started
+// from the extrapolation 2 u^n - u^{n-1}, to a relative 1e-13.  FP64; the
+// levels are host-driven (two synchronisations per inner iteration), so
+// this path is not captured in graphs.
+// ---------------------------------------------------------------------------
+ewh_status mdot_dev(ewh_ctx* ctx, const double* x, const double* y, double* out_dev);
+constexpr int I_RR = 0, I_PQ = 1, I_GG = 2, I_N = 3;
+
+// dst = M^{-1} K src (dense FP64 vectors)
+ewh_status implicit_minvK(ewh_ctx* ctx, const double* src, double* dst) {
+  Wave<double>& w = ctx->w64;
+  EWH_CU(launch_pack<double>(ctx->g, src, w.u_a, ctx->st));
+  EWH_CU(launch_minvK<double>(ctx->g, ctx->order, w.u_a, w.u_b, w.lam, w.mu, w.irh2, w.sigma, ctx->st,
+                              &ctx->launches));
+  EWH_CU(launch_unpack<double>(ctx->g, w.u_b, dst, nullptr, ctx->st));
+  ctx->launches += 2;
+  return EWH_OK;
+}
+
+// dst = B src
+ewh_status implicit_B(ewh_ctx* ctx, const double* src, double* dst) {
+  ewh_status s = implicit_minvK(ctx, src, dst);
+  if (s != EWH_OK) return s;
+  EWH_CU(launch_axpby(total_unknowns(ctx), 1.0, src, 0.5 * ctx->dt * ctx->dt, dst, ctx->st));
+  ctx->launches += 1;
+  return EWH_OK;
+}
+
+// per-rhs M-dots into iscal[which][rhs], copied to the host
+ewh_status implicit_dot(ewh_ctx* ctx, const double* x, const double* y, int which, std::vector<double>& out) {
+  const int R = ctx->g.nrhs;
+  ewh_status s = mdot_dev(ctx, x, y, ctx->iscal + (size_t)which * R);
+  if (s != EWH_OK) return s;
+  EWH_CU(cudaMemcpyAsync(out.data(), ctx->iscal + (size_t)which * R, sizeof(double) * R, cudaMemcpyDeviceToHost,
+                         ctx->st));
+  EWH_CU(cudaStreamSynchronize(ctx->st));
+  return EWH_OK;
+}
+
+// Solve B x = g (x holds the starting guess) by CG in the M inner product.
+ewh_status implicit_solve(ewh_ctx* ctx, const double* gv, double* x) {
+  const int R = ctx->g.nrhs;
+  const long long n = total_unknowns(ctx), seg = n / R;
+  std::vector<double> rr(R), pq(R), gg(R), rr_new(R);
+  ewh_status s = implicit_B(ctx, x, ctx->iq);
+  if (s != EWH_OK) return s;
+  EWH_CU(cudaMemcpyAsync(ctx->ir, gv, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->st));
+  EWH_CU(launch_axpby(n, -1.0, ctx->iq, 1.0, ctx->ir, ctx->st));
+  EWH_CU(cudaMemcpyAsync(ctx->ip, ctx->ir, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->st));
+  s = implicit_dot(ctx, gv, gv, I_GG, gg);
+  if (s != EWH_OK) return s;
+  s = implicit_dot(ctx, ctx->ir, ctx->ir, I_RR, rr);
+  if (s != EWH_OK) return s;
+  const double tol2 = 1e-26;
+  for (int it = 0;; ++it) {
+    bool done = true;
+    for (int k = 0; k < R; ++k) done = done && (rr[k] <= tol2 * gg[k]);
+    if (done) return EWH_OK;
+    if (it >= 5000) return fail(ctx, EWH_ENOTCONV, "implicit level: inner CG did not converge in 5000 iterations");
+    s = implicit_B(ctx, ctx->ip, ctx->iq);
+    if (s != EWH_OK) return s;
+    s = implicit_dot(ctx, ctx->ip, ctx->iq, I_PQ, pq);
+    if (s != EWH_OK) return s;
+    for (int k = 0; k < R; ++k) {
+      if (rr[k] <= tol2 * gg[k]) continue;
+      if (!(pq[k] > 0.0)) return fail(ctx, EWH_EBREAKDOWN, "implicit level: inner CG lost definiteness");
+      const double a = rr[k] / pq[k];
+      EWH_CU(launch_axpby(seg, a, ctx->ip + k * seg, 1.0, x + k * seg, ctx->st));
+      EWH_CU(launch_axpby(seg, -a, ctx->iq + k * seg, 1.0, ctx->ir + k * seg, ctx->st));
+    }
+    s = implicit_dot(ctx, ctx->ir, ctx->ir, I_RR, rr_new);
+    if (s != EWH_OK) return s;
+    for (int k = 0; k < R; ++k) {
+      if (rr[k] <= tol2 * gg[k]) continue;
+      EWH_CU(launch_axpby(seg, 1.0, ctx->ir + k * seg, rr_new[k] / rr[k], ctx->ip + k * seg, ctx->st));
+      rr[k] = rr_new[k];
+    }
+    ++ctx->inner_iters;
+  }
+}
+
+// acc = Pi u0 (forced) or S u0: all levels of the implicit scheme; u0 dense or
+// null (zero).  The result is left in ctx->iacc.
+ewh_status implicit_wave(ewh_ctx* ctx, const double* u0, bool forced) {
+  const long long n = total_unknowns(ctx);
+  const double dt = ctx->dt, c = 0.5 * dt * dt, cdt = std::cos(ctx->omega * dt);
+  if (forced && !ctx->ifr) return fail(ctx, EWH_EINVAL, "problem was created without forcing");
+  if (u0) EWH_CU(cudaMemcpyAsync(ctx->iu, u0, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->st));
+  else EWH_CU(cudaMemsetAsync(ctx->iu, 0, sizeof(double) * n, ctx->st));
+  // B u^{-1} = (alpha/2) u^0 - c (f/rho) cos(w dt); start from u^0
+  EWH_CU(cudaMemsetAsync(ctx->ig, 0, sizeof(double) * n, ctx->st));
+  EWH_CU(launch_axpby(n, 0.5 * ctx->alpha, ctx->iu, 0.0, ctx->ig, ctx->st));
+  if (forced) EWH_CU(launch_axpby(n, -c * cdt, ctx->ifr, 1.0, ctx->ig, ctx->st));
+  EWH_CU(cudaMemcpyAsync(ctx->iu_prev, ctx->iu, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->st));
+  ewh_status s = implicit_solve(ctx, ctx->ig, ctx->iu_prev);
+  if (s != EWH_OK) return s;
+  // acc = w_0 u^0
+  EWH_CU(cudaMemsetAsync(ctx->iacc, 0, sizeof(double) * n, ctx->st));
+  EWH_CU(launch_axpby(n, ctx->weights[0], ctx->iu, 0.0, ctx->iacc, ctx->st));
+  const int N = ctx->nt * ctx->periods;
+  for (int lev = 0; lev < N; ++lev) {
+    // g = alpha u^n - B u^{n-1} - dt^2 (f/rho) cos(w t_n) cos(w dt)
+    s = implicit_B(ctx, ctx->iu_prev, ctx->ig);
+    if (s != EWH_OK) return s;
+    EWH_CU(launch_axpby(n, ctx->alpha, ctx->iu, -1.0, ctx->ig, ctx->st));
+    if (forced) {
+      const double cn = std::cos(2.0 * M_PI * (double)(lev % ctx->nt) / (double)ctx->nt);
+      EWH_CU(launch_axpby(n, -dt * dt * cn * cdt, ctx->ifr, 1.0, ctx->ig, ctx->st));
+    }
+    // start from 2 u^n - u^{n-1}
+    EWH_CU(cudaMemcpyAsync(ctx->iu_next, ctx->iu_prev, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->st));
+    EWH_CU(launch_axpby(n, 2.0, ctx->iu, -1.0, ctx->iu_next, ctx->st));
+    s = implicit_solve(ctx, ctx->ig, ctx->iu_next);
+    if (s != EWH_OK) return s;
+    double* t = ctx->iu_prev;
+    ctx->iu_prev = ctx->iu;
+    ctx->iu = ctx->iu_next;
+    ctx->iu_next = t;
+    EWH_CU(launch_axpby(n, ctx->weights[lev + 1], ctx->iu, 1.0, ctx->iacc, ctx->st));
+    ctx->launches += 4;
+  }
+  return EWH_OK;
+}
+
+// v_out = S v_in (sub_from null) or sub_from - S v_in, implicit scheme
+ewh_status implicit_S(ewh_ctx* ctx, const double* v_in, double* v_out, const double* sub_from) {
+  const long long n = total_unknowns(ctx);
+  ewh_status s = implicit_wave(ctx, v_in, false);
+  if (s != EWH_OK) return s;
+  if (sub_from) {
+    if (sub_from != v_out) EWH_CU(cudaMemcpyAsync(v_out, sub_from, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->st));
+    EWH_CU(launch_axpby(n, -1.0, ctx->iacc, 1.0, v_out, ctx->st));
+  } else {
+    EWH_CU(cudaMemcpyAsync(v_out, ctx->iacc, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->st));
+  }
+  return EWH_OK;
+}
+
 template <typename T>
 ewh_status apply_S_T(ewh_ctx* ctx, const double* v_in, double* v_out, const double* sub_from) {
+  if (ctx->implicit) return implicit_S(ctx, v_in, v_out, sub_from);
   ewh_status s = run_wave<T>(ctx, v_in, false);
   if (s != EWH_OK) return s;
   EWH_CU(launch_unpack<T>(ctx->g, wave_of<T>(ctx).acc, v_out, sub_from, ctx->st));
@@ -669,7 +821,7 @@ template <typename T>
 ewh_status cg_begin(ewh_ctx* ctx, double* r, double tol, double drop, CgState& cs) {
   const int R = ctx->g.nrhs;
   const long long n = total_unknowns(ctx);
-  ewh_status st = ensure_graph<T>(ctx, false);
+  ewh_status st = ctx->implicit ? EWH_OK : ensure_graph<T>(ctx, false);  // implicit: no step graph
   if (st != EWH_OK) return st;
   st = mdot_dev(ctx, r, r, sc(ctx, S_RR));
   if (st != EWH_OK) return st;
@@ -708,7 +860,10 @@ ewh_status cg_enqueue_iteration(ewh_ctx* ctx, double* x, double* r, bool direct_
   // p = r + beta p ; u^0 = p
   EWH_CU(launch_pupdate_pack<T>(g, r, ctx->kp, sc(ctx, S_BETA), w.u_a, ctx->st));
   ctx->launches += 1;
-  if (direct_steps) {
+  if (ctx->implicit) {  // q = p - S p by the implicit levels
+    ewh_status s = implicit_S(ctx, ctx->kp, ctx->kq, ctx->kp);
+    if (s != EWH_OK) return s;
+  } else if (direct_steps) {
     long long count = 0;
     EWH_CU(enqueue_steps<T>(ctx, w, false, &count));
     ctx->launches += count;
@@ -717,7 +872,7 @@ ewh_status cg_enqueue_iteration(ewh_ctx* ctx, double* x, double* r, bool direct_
     ctx->launches += w.graph_S_kernels;
   }
   // q = p - S p
-  EWH_CU(launch_unpack<T>(g, w.acc, ctx->kq, ctx->kp, ctx->st));
+  if (!ctx->implicit) EWH_CU(launch_unpack<T>(g, w.acc, ctx->kq, ctx->kp, ctx->st));
   EWH_CU(launch_mdot_partial(g, ctx->mw, ctx->kp, ctx->kq, ctx->part, ctx->st));
   EWH_CU(launch_cg_alpha(R, ctx->part, ctx->nblk, sc(ctx, S_RR), sc(ctx, S_ALPHA), ctx->active, ctx->flags,
                          ctx->st));
@@ -811,6 +966,7 @@ ewh_status run_cg(ewh_ctx* ctx, double* x, double* r, double tol, int maxit, dou
 // residual only.
 template <typename T>
 ewh_status ar_apply(ewh_ctx* ctx, double* src, double* dst) {
+  if (ctx->implicit) return implicit_S(ctx, src, dst, src);
   Wave<T>& w = wave_of<T>(ctx);
   EWH_CU(launch_pack<T>(ctx->g, src, w.u_a, ctx->st));
   EWH_CU(launch_timed_graph<T>(ctx, w.graph_S));
@@ -839,7 +995,7 @@ ewh_status run_cr(ewh_ctx* ctx, double* x, double* r, double tol, int maxit, dou
                   double* rel_out) {
   const Geom& g = ctx->g;
   const int R = g.nrhs;
-  ewh_status st = ensure_graph<T>(ctx, false);
+  ewh_status st = ctx->implicit ? EWH_OK : ensure_graph<T>(ctx, false);  // implicit: no step graph
   if (st != EWH_OK) return st;
   // true residual norms and active mask
   st = mdot_dev(ctx, r, r, sc(ctx, S_RR));
@@ -945,7 +1101,7 @@ ewh_status run_minres(ewh_ctx* ctx, double* x, double* r, double tol, int maxit,
   const int R = g.nrhs;
   const long long n = total_unknowns(ctx);
   const long long seg = n / R;  // unknowns of one right-hand side
-  ewh_status st = ensure_graph<T>(ctx, false);
+  ewh_status st = ctx->implicit ? EWH_OK : ensure_graph<T>(ctx, false);  // implicit: no step graph
   if (st != EWH_OK) return st;
   double* v_prev = ctx->kp;
   double* v = ctx->kq;
@@ -1081,9 +1237,16 @@ ewh_status solve_impl(ewh_ctx* ctx, double tol, int maxit, const double* x0, dou
   const long long n = total_unknowns(ctx);
   ctx->history.clear();
   // b = Pi 0 in FP64: the right-hand side every residual is measured against
-  ewh_status s = run_wave<double>(ctx, nullptr, true);
-  if (s != EWH_OK) return s;
-  EWH_CU(launch_unpack<double>(g, ctx->w64.acc, ctx->kb, nullptr, ctx->st));
+  ewh_status s = EWH_OK;
+  if (ctx->implicit) {
+    s = implicit_wave(ctx, nullptr, true);
+    if (s != EWH_OK) return s;
+    EWH_CU(cudaMemcpyAsync(ctx->kb, ctx->iacc, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->st));
+  } else {
+    s = run_wave<double>(ctx, nullptr, true);
+    if (s != EWH_OK) return s;
+    EWH_CU(launch_unpack<double>(g, ctx->w64.acc, ctx->kb, nullptr, ctx->st));
+  }
   ctx->launches += 1;
   inf->s_applies_fp64 += 1;
   s = mdot_dev(ctx, ctx->kb, ctx->kb, sc(ctx, S_BB));
@@ -1159,6 +1322,9 @@ ewh_status validate_desc(const ewh_grid_desc* d, int nrhs) {
   if (d->periods < 1 || d->periods > 1000) return fail(nullptr, EWH_EINVAL, "periods must be in [1, 1000]");
   if (d->nt < 0 || (d->nt > 0 && d->nt < 5)) return fail(nullptr, EWH_EINVAL, "nt must be 0 or >= 5");
   if (nrhs < 1 || nrhs > 65535) return fail(nullptr, EWH_EINVAL, "nrhs must be in [1, 65535]");
+  if (d->implicit != 0 && d->implicit != 1) return fail(nullptr, EWH_EINVAL, "implicit must be 0 or 1");
+  if (d->implicit && (d->precision != EWH_FP64 || d->nt < 5))
+    return fail(nullptr, EWH_EINVAL, "the implicit scheme needs precision EWH_FP64 and an explicit nt >= 5");
   return EWH_OK;
 }
 
@@ -1350,6 +1516,9 @@ void ewh_destroy(ewh_ctx* ctx) {
   cudaFree(ctx->ktmp);
   cudaFree(ctx->kar);
   cudaFree(ctx->kap);
+  for (double* q : {ctx->iu_prev, ctx->iu, ctx->iu_next, ctx->ig, ctx->ir, ctx->ip, ctx->iq, ctx->iacc, ctx->ifr,
+                    ctx->iscal})
+    cudaFree(q);
   cudaFree(ctx->mw);
   cudaFree(ctx->part);
   cudaFree(ctx->scal);
@@ -1463,6 +1632,17 @@ ewh_status ewh_create(const ewh_grid_desc* desc, const double* rho, const double
     ctx->weights[k] = (2.0 / N) * eta * (std::cos(2.0 * M_PI * k / nt) - 0.25);
   }
   ctx->has_forcing = forcing != nullptr;
+  if (desc->implicit) {  // Section 4.4: alpha (eq. alpha), or 2 for the unmodified scheme
+    const double wd = omega * ctx->dt;
+    ctx->implicit = 1;
+    ctx->alpha = ctx->corrected ? std::cos(wd) * (2.0 + wd * wd) : 2.0;
+    ctx->omega_t = std::cos(wd) > 0.0 ? 2.0 * std::sin(wd / 2.0) / (ctx->dt * std::sqrt(std::cos(wd))) : NAN;
+    ctx->kt = 0.0;
+    if (!(std::fabs(ctx->alpha) < 2.0) && ctx->corrected) {
+      delete ctx;
+      return fail(nullptr, EWH_EINVAL, "implicit scheme unstable: |alpha| >= 2 (use nt >= 5)");
+    }
+  }
 
   // CUDA resources
   auto bail = [&](ewh_status s, const std::string& m) {
@@ -1512,10 +1692,21 @@ ewh_status ewh_create(const ewh_grid_desc* desc, const double* rho, const double
          cudaMallocHost(&ctx->h_scal, sizeof(double) * S_N * nrhs) == cudaSuccess &&
          cudaMallocHost(&ctx->h_act, sizeof(int) * nrhs) == cudaSuccess &&
          cudaMallocHost(&ctx->h_flag, sizeof(int)) == cudaSuccess;
+    if (ok && ctx->implicit) {
+      for (double** q : {&ctx->iu_prev, &ctx->iu, &ctx->iu_next, &ctx->ig, &ctx->ir, &ctx->ip, &ctx->iq, &ctx->iacc})
+        ok = ok && alloc_zero(q, n) == cudaSuccess;
+      ok = ok && alloc_zero(&ctx->iscal, (size_t)I_N * nrhs) == cudaSuccess;
+      if (ok && forcing) ok = alloc_zero(&ctx->ifr, n) == cudaSuccess;
+    }
     if (!ok) {
       cudaGetLastError();
       s = fail(ctx, EWH_ENOMEM, "device allocation of the Krylov workspace failed");
     }
+  }
+  if (s == EWH_OK && ctx->ifr) {  // f / rho at the unknowns, dense (from the padded FP64 field)
+    if (launch_unpack<double>(g, ctx->w64.frho, ctx->ifr, nullptr, ctx->st) != cudaSuccess)
+      s = fail(ctx, EWH_ECUDA, "forcing unpack failed");
+    ctx->launches += 1;
   }
   if (s == EWH_OK) {
     if (launch_fill_mass(g, ctx->order, d_r, desc->h, ctx->mw, ctx->st) != cudaSuccess)
@@ -1580,7 +1771,12 @@ ewh_status ewh_apply_Pi0(ewh_ctx* ctx, double* b_out) {
   ewh_status s = check_async(ctx);
   if (s != EWH_OK) return s;
   enter(ctx);
-  if (ctx->precision == EWH_FP64) {
+  if (ctx->implicit) {
+    s = implicit_wave(ctx, nullptr, true);
+    if (s == EWH_OK && cudaMemcpyAsync(b_out, ctx->iacc, sizeof(double) * total_unknowns(ctx),
+                                       cudaMemcpyDeviceToDevice, ctx->st) != cudaSuccess)
+      s = fail(ctx, EWH_ECUDA, "copy failed");
+  } else if (ctx->precision == EWH_FP64) {
     s = run_wave<double>(ctx, nullptr, true);
     if (s == EWH_OK && launch_unpack<double>(ctx->g, ctx->w64.acc, b_out, nullptr, ctx->st) != cudaSuccess)
       s = fail(ctx, EWH_ECUDA, "unpack launch failed");
@@ -1720,6 +1916,8 @@ ewh_status ewh_batch_create(const ewh_problem* probs, int nprob, void* cuda_stre
   ewh_batch* b = new ewh_batch();
   b->user_stream = (cudaStream_t)cuda_stream;
   b->precision = probs[0].desc.precision;
+  for (int k = 0; k < nprob; ++k)
+    if (probs[k].desc.implicit) return fail(nullptr, EWH_EINVAL, "batch members must use the explicit scheme");
   for (int k = 0; k < nprob; ++k) {
     ewh_ctx* c = nullptr;
     ewh_status s = ewh_create(&probs[k].desc, probs[k].rho, probs[k].lambda, probs[k].mu, probs[k].omega,

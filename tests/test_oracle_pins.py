@@ -651,3 +651,22 @@ def test_implicit_krylov_solves():
     assert info.converged and np.linalg.norm(x - v) <= 1e-9 * np.linalg.norm(v)
     xm, im = O.minres_solve(s, tol=1e-11, maxit=500)
     assert im.converged and np.linalg.norm(xm - v) <= 1e-9 * np.linalg.norm(v)
+
+
+def test_implicit_few_steps_is_indefinite_and_minres_solves_it():
+    """The situation of the Section 4.4 remark: the implicit scheme with five
+    steps per period makes M(I - S) indefinite (dense-S eigenvalues), and
+    MINRES still reaches the discrete Helmholtz solution, monotonically."""
+    p = inputs.small_problem(2, [6, 5], 2, [0, 1, 0, 0], seed=3, omega=7.5)
+    p.implicit = 1
+    s = O.build_system(p, nt=5)
+    S = O.form_S(s)
+    mh = np.sqrt(s.Mdiag)
+    a_sym = ((np.eye(S.shape[0]) - S) * mh[:, None]) / mh[None, :]
+    ev = np.linalg.eigvalsh(0.5 * (a_sym + a_sym.T))
+    assert ev.min() < -1e-3 < 1e-3 < ev.max()
+    v = O.helmholtz_direct(s)
+    x, info = O.minres_solve(s, tol=1e-11, maxit=500)
+    assert info.converged
+    assert np.linalg.norm(x - v) <= 1e-8 * np.linalg.norm(v)
+    assert np.all(np.diff(info.history) <= 1e-14)
