@@ -24,6 +24,7 @@ What it computes, in the paper's order and notation:
   in the Section 4.5 remark; MINRES as in the Section 4.4 remark on indefinite
   systems).
 * Section 4.4: the implicit (corrected) scheme, each level a sparse solve.
+* Section 4.1, curvilinear form: mapped 2D grids (order 4), ``assemble_mapped``.
 * Appendix B: the discrete filter transfer function beta_h.
 
 Parity is pinned by tests/test_oracle_*.py against closed forms, invariants,
@@ -265,6 +266,73 @@ def assemble(dim, n, h, order, bc, rho, lam, mu):
     return K, Mdiag, Wdiag, rho_u, sel
 
 
+def mapped_metrics(n, h, X, Y):
+    """Metric terms of a smooth mapping x(q, r), y(q, r) sampled on the node
+    grid (q, r) = (i h, j h) (Section 4.1, curvilinear form): x_q, x_r, y_q,
+    y_r from the fourth-order SBP derivative, J = x_q y_r - x_r y_q and
+    q_x = y_r / J, q_y = -x_r / J, r_x = -y_q / J, r_y = x_q / J (flattened,
+    C order y, x).  Returns (J, qx, qy, rx, ry)."""
+    Dq = _along(0, sbp4_first_derivative(n[0])[0], n) / h
+    Dr = _along(1, sbp4_first_derivative(n[1])[0], n) / h
+    x, y = X.reshape(-1), Y.reshape(-1)
+    xq, xr, yq, yr = Dq @ x, Dr @ x, Dq @ y, Dr @ y
+    J = xq * yr - xr * yq
+    return J, yr / J, -xr / J, -yq / J, xq / J
+
+
+def assemble_mapped(n, h, bc, rho, lam, mu, X, Y):
+    """K (= -L_h) and M on the unknowns for a 2D curvilinear grid, order 4
+    (Section 4.1, curvilinear form; the energy reading of the Cartesian case
+    carried over): the energy density 1/2 [lambda (div u)^2 + 2 mu eps:eps]
+    with physical derivatives d/dx = q_x d/dq + r_x d/dr, d/dy = q_y d/dq +
+    r_y d/dr (SBP D in q and r), summed with the weight H J h^2; the mass is
+    rho J H h^2 (the paper's rho J).  With X = q, Y = r it is the Cartesian
+    order-4 operator."""
+    dim = 2
+    nn = int(np.prod(n))
+    J, qx, qy, rx, ry = mapped_metrics(n, h, X, Y)
+    d0, h0 = sbp4_first_derivative(n[0])
+    d1, h1 = sbp4_first_derivative(n[1])
+    Dq = _along(0, d0, n) / h
+    Dr = _along(1, d1, n) / h
+    Dx = sp.diags(qx) @ Dq + sp.diags(rx) @ Dr
+    Dy = sp.diags(qy) @ Dq + sp.diags(ry) @ Dr
+    Ds = [Dx.tocsr(), Dy.tocsr()]
+    weight = _outer([h0, h1])
+    wJ = weight * J * h ** 2
+    HL = sp.diags(wJ * lam.reshape(-1))
+    HM = sp.diags(wJ * mu.reshape(-1))
+    blocks = [[None] * dim for _ in range(dim)]
+    for al in range(dim):
+        for be in range(dim):
+            Kab = Ds[al].T @ HL @ Ds[be] + Ds[be].T @ HM @ Ds[al]
+            if al == be:
+                for b in range(dim):
+                    Kab = Kab + Ds[b].T @ HM @ Ds[b]
+            blocks[al][be] = Kab
+    Kfull = sp.bmat(blocks, format="csr")
+    axk = [axis_unknown(n[a], bc[2 * a], bc[2 * a + 1]) for a in range(dim)]
+    known = _outer([k.astype(float) for k in axk]) > 0.5
+    sel = np.nonzero(known)[0]
+    sel_all = np.concatenate([sel + c * nn for c in range(dim)])
+    K = Kfull[sel_all][:, sel_all].tocsr()
+    rho_f = rho.reshape(-1)
+    Mdiag = np.tile(rho_f[sel] * wJ[sel], dim)
+    Wdiag = np.tile(wJ[sel], dim)
+    rho_u = np.tile(rho_f[sel], dim)
+    return K, Mdiag, Wdiag, rho_u, sel
+
+
+def cfl_dt_mapped(n, h, cfl, rho, lam, mu, X, Y):
+    """Time-step bound on a mapped grid: dt = cfl h / sqrt(max over nodes of
+    (lambda + 3 mu)/rho * (|grad q|^2 + |grad r|^2) / 2); the Cartesian bound
+    when the mapping is the identity."""
+    J, qx, qy, rx, ry = mapped_metrics(n, h, X, Y)
+    s2 = (qx * qx + qy * qy + rx * rx + ry * ry) / 2.0
+    c2 = ((lam + 3 * mu) / rho).reshape(-1)
+    return cfl * h / math.sqrt(np.max(c2 * s2))
+
+
 def cfl_dt(dim, order, h, cfl, rho, lam, mu):
     """Time-step bound dt_CFL = cfl * h / sqrt(max over nodes of (lambda + (d+1) mu) / rho).
 
@@ -288,7 +356,13 @@ def build_system(prob, nt: Optional[int] = None) -> System:
     """Medium + grid + forcing -> System (reading of Sections 2.1, 4.1, 4.3)."""
     dim, n, h, order = prob.dim, list(prob.n), prob.h, prob.order
     bc = list(prob.bc)
-    K, Mdiag, Wdiag, rho_u, sel = assemble(dim, n, h, order, bc, prob.rho, prob.lam, prob.mu)
+    mapping = getattr(prob, "mapping", None)
+    if mapping is not None:
+        if dim != 2 or order != 4:
+            raise ValueError("mapped grids: 2D, order 4")
+        K, Mdiag, Wdiag, rho_u, sel = assemble_mapped(n, h, bc, prob.rho, prob.lam, prob.mu, *mapping)
+    else:
+        K, Mdiag, Wdiag, rho_u, sel = assemble(dim, n, h, order, bc, prob.rho, prob.lam, prob.mu)
     s = System(dim=dim, n=n, h=h, order=order, bc=bc, omega=prob.omega)
     s.K, s.Mdiag, s.Wdiag, s.rho_u, s.sel = K, Mdiag, Wdiag, rho_u, sel
     nn = int(np.prod(n))
@@ -297,7 +371,8 @@ def build_system(prob, nt: Optional[int] = None) -> System:
     s.f_over_rho = f / rho_u[None, :]
     T = 2.0 * math.pi / prob.omega
     if nt is None:
-        dtc = cfl_dt(dim, order, h, prob.cfl, prob.rho, prob.lam, prob.mu)
+        dtc = (cfl_dt_mapped(n, h, prob.cfl, prob.rho, prob.lam, prob.mu, *mapping) if mapping is not None
+               else cfl_dt(dim, order, h, prob.cfl, prob.rho, prob.lam, prob.mu))
         nt = max(5, int(math.ceil(T / dtc)))
     s.nt = nt
     s.periods = prob.periods

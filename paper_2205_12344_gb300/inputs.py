@@ -21,7 +21,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import List, Sequence
+from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -48,6 +48,7 @@ class Problem:
     periods: int = 1
     corrected: int = 1
     implicit: int = 0       # 1: implicit time stepping (needs an explicit nt >= 5)
+    mapping: Optional[Tuple[np.ndarray, np.ndarray]] = None  # (x, y) node coordinates: mapped 2D grid
 
     @property
     def nrhs(self) -> int:

@@ -670,3 +670,103 @@ def test_implicit_few_steps_is_indefinite_and_minres_solves_it():
     assert info.converged
     assert np.linalg.norm(x - v) <= 1e-8 * np.linalg.norm(v)
     assert np.all(np.diff(info.history) <= 1e-14)
+
+
+# ---------------------------------------------------------------- curvilinear grids (Section 4.1)
+
+def _grid_coords(n, h):
+    return np.meshgrid(np.arange(n[0]) * h, np.arange(n[1]) * h)
+
+
+def _annulus(n, h, span=math.pi / 3, r0=1.0, dr=0.5):
+    """Annular sector, radius along q and angle along r (so J > 0):
+    x = (r0 + dr q') cos(span r'), y = (r0 + dr q') sin(span r'), q', r' in [0, 1]."""
+    Q, R = _grid_coords(n, h)
+    rad = r0 + dr * Q / (h * (n[0] - 1))
+    ang = span * R / (h * (n[1] - 1))
+    return rad * np.cos(ang), rad * np.sin(ang)
+
+
+def test_mapped_identity_is_cartesian():
+    """With x = q, y = r the mapped assembly is the Cartesian order-4 operator."""
+    p = inputs.small_problem(2, [10, 9], 4, [0, 1, 1, 0, 0, 0], seed=4)
+    Q, R = _grid_coords(p.n, p.h)
+    K1, M1, W1, _, _ = O.assemble(2, p.n, p.h, 4, p.bc, p.rho, p.lam, p.mu)
+    K2, M2, W2, _, _ = O.assemble_mapped(p.n, p.h, p.bc, p.rho, p.lam, p.mu, Q, R)
+    assert abs(K1 - K2).max() <= 1e-13 * abs(K1).max()
+    assert np.abs(M1 - M2).max() <= 1e-14 * M1.max() and np.abs(W1 - W2).max() <= 1e-14 * W1.max()
+    p.mapping = (Q, R)
+    p2 = inputs.small_problem(2, [10, 9], 4, [0, 1, 1, 0, 0, 0], seed=4)
+    assert O.build_system(p).nt == O.build_system(p2).nt
+
+
+def test_mapped_affine_rigid_modes_and_psd():
+    """On an affine (rotated, scaled, shifted) grid with every side free, the
+    physical rigid motions (two translations, the rotation (-y, x)) are in the
+    kernel of K to rounding, and K is symmetric positive semi-definite with
+    exactly that 3-dimensional kernel."""
+    p = inputs.small_problem(2, [10, 9], 4, [1, 1, 1, 1, 0, 0], seed=4)
+    Q, R = _grid_coords(p.n, p.h)
+    th, sc = 0.3, 1.7
+    X = sc * (math.cos(th) * Q - math.sin(th) * R) + 0.2
+    Y = sc * (math.sin(th) * Q + math.cos(th) * R) - 0.1
+    K, M, W, _, sel = O.assemble_mapped(p.n, p.h, p.bc, p.rho, p.lam, p.mu, X, Y)
+    x, y = X.reshape(-1)[sel], Y.reshape(-1)[sel]
+    for u in (np.concatenate([np.ones_like(x), 0 * x]), np.concatenate([0 * x, np.ones_like(x)]),
+              np.concatenate([-y, x])):
+        assert np.abs(K @ u).max() <= 1e-12 * abs(K).max()
+    Kd = K.toarray()
+    assert np.abs(Kd - Kd.T).max() <= 1e-14 * np.abs(Kd).max()
+    ev = np.linalg.eigvalsh(Kd)
+    assert ev.min() >= -1e-12 * ev.max()
+    assert np.sum(np.abs(ev) < 1e-10 * ev.max()) == 3
+
+
+def test_mapped_interior_truncation_fourth_order():
+    """On a curved sector grid, M^{-1} K u at interior nodes (9 or more nodes
+    from every side) approximates -(1/rho) div sigma(u) of a smooth field to
+    fourth order: (lambda + mu) grad div u + mu Lap u, written out by hand."""
+    lam0, mu0 = 2.0, 1.0
+
+    def exact(x, y):
+        dxdiv = -0.3 * np.sin(x) * np.cos(y) - 0.4 * np.sin(2 * x) * np.cos(y)
+        dydiv = -0.3 * np.cos(x) * np.sin(y) - 0.2 * np.cos(2 * x) * np.sin(y)
+        lapu = -0.6 * np.sin(x) * np.cos(y)
+        lapv = -1.0 * np.cos(2 * x) * np.sin(y)
+        return (lam0 + mu0) * dxdiv + mu0 * lapu, (lam0 + mu0) * dydiv + mu0 * lapv
+
+    errs = []
+    for m in (33, 65):
+        n = [m, m]
+        h = 1.0 / (m - 1)
+        X, Y = _annulus(n, h)
+        ones = np.ones((m, m))
+        K, M, W, rho_u, sel = O.assemble_mapped(n, h, [1, 1, 1, 1], ones, lam0 * ones, mu0 * ones, X, Y)
+        x, y = X.reshape(-1)[sel], Y.reshape(-1)[sel]
+        u = np.concatenate([0.3 * np.sin(x) * np.cos(y), 0.2 * np.cos(2 * x) * np.sin(y)])
+        got = -(K @ u) / M
+        ex, ey = exact(x, y)
+        ii, jj = np.meshgrid(np.arange(m), np.arange(m))
+        inner = ((ii >= 9) & (ii <= m - 10) & (jj >= 9) & (jj <= m - 10)).reshape(-1)[sel]
+        nn = len(sel)
+        err = max(np.abs(got[:nn] - ex)[inner].max(), np.abs(got[nn:] - ey)[inner].max())
+        errs.append(err)
+    rate = math.log2(errs[0] / errs[1])
+    assert rate > 3.6, (errs, rate)
+
+
+def test_mapped_cfl_stable_and_fixed_point():
+    """On the sector grid with cfl = 0.5 the leapfrog bound c dt^2 rho(M^{-1} K) < 4
+    holds with margin, and the Helmholtz solution is a fixed point of Pi."""
+    p = inputs.small_problem(2, [12, 12], 4, [0, 1, 0, 0, 0, 0], seed=9)
+    n = p.n
+    h = 1.0 / (n[0] - 1)
+    p.h = h
+    p.mapping = _annulus(n, h)
+    s = O.build_system(p)
+    ms = np.sqrt(s.Mdiag)
+    top = np.linalg.eigvalsh(s.K.toarray() / ms[:, None] / ms[None, :]).max()
+    assert O.mapped_metrics(n, h, *p.mapping)[0].min() > 0
+    assert s.kt * top < 2.0
+    v = O.helmholtz_direct(s)
+    assert np.linalg.norm(O.apply_Pi(s, v) - v) <= 1e-11 * np.linalg.norm(v)
