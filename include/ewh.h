@@ -138,6 +138,24 @@ ewh_status ewh_create(const ewh_grid_desc* desc, const double* rho, const double
                       const double* mu, double omega, const double* forcing, int nrhs,
                       void* cuda_stream, ewh_ctx** out);
 
+/* Create a problem on a curvilinear 2D grid (Section 4.1, curvilinear form).
+ * The nodes are the image of (q, r) = (i h, j h), i < n[0], j < n[1], under a
+ * smooth mapping: x, y (host or device, one double per node, i fastest; copied)
+ * are its coordinates there.  The metric terms x_q, x_r, y_q, y_r come from the
+ * order-4 SBP derivative in q and r, J = x_q y_r - x_r y_q; the operator is the
+ * energy form with physical derivatives q_x D_q + r_x D_r (and y alike), the
+ * mass rho J H h^2, and dt uses max (lambda + 3 mu)/rho (|grad q|^2 + |grad r|^2)/2.
+ * Boundary conditions apply to the sides of the (q, r) square.  The other
+ * arguments are as for ewh_create; the identity mapping gives the Cartesian
+ * problem.  Requires dim 2 and order 4 (else EWH_EINVAL) and J > 0 at every
+ * node (EWH_EINVAL naming the first node where it fails); EWH_ECUDA when no
+ * device is present (the metric terms are computed on the device).  Mapped
+ * contexts always use the per-level two-kernel step and cannot join a batch. */
+ewh_status ewh_create_mapped(const ewh_grid_desc* desc, const double* x, const double* y,
+                             const double* rho, const double* lambda, const double* mu,
+                             double omega, const double* forcing, int nrhs, void* cuda_stream,
+                             ewh_ctx** out);
+
 /* Fill *info with the problem's scalars. */
 ewh_status ewh_get_info(const ewh_ctx* ctx, ewh_problem_info* info);
 

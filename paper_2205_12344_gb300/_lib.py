@@ -52,6 +52,8 @@ _D = ctypes.POINTER(ctypes.c_double)
 SIGNATURES = {
     "ewh_create": (ctypes.c_int, [ctypes.POINTER(ewh_grid_desc), _P, _P, _P, ctypes.c_double, _P, ctypes.c_int,
                                   _P, ctypes.POINTER(_P)]),
+    "ewh_create_mapped": (ctypes.c_int, [ctypes.POINTER(ewh_grid_desc), _P, _P, _P, _P, _P, ctypes.c_double, _P,
+                                         ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "ewh_get_info": (ctypes.c_int, [_P, ctypes.POINTER(ewh_problem_info)]),
     "ewh_apply_S": (ctypes.c_int, [_P, _P, _P]),
     "ewh_apply_S_fp64": (ctypes.c_int, [_P, _P, _P]),
@@ -153,6 +155,15 @@ def ewh_create(desc, rho, lam, mu, omega, forcing, nrhs, stream=None):
     st = ctypes.c_void_p(stream) if stream else None
     _check(lib.ewh_create(ctypes.byref(desc), _ptr(rho), _ptr(lam), _ptr(mu), float(omega), _ptr(forcing),
                           int(nrhs), st, ctypes.byref(out)))
+    return out
+
+
+def ewh_create_mapped(desc, x, y, rho, lam, mu, omega, forcing, nrhs, stream=None):
+    lib = load()
+    out = ctypes.c_void_p()
+    st = ctypes.c_void_p(stream) if stream else None
+    _check(lib.ewh_create_mapped(ctypes.byref(desc), _ptr(x), _ptr(y), _ptr(rho), _ptr(lam), _ptr(mu), float(omega),
+                                 _ptr(forcing), int(nrhs), st, ctypes.byref(out)))
     return out
 
 

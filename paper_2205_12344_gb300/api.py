@@ -47,7 +47,13 @@ class WaveHoltz:
         mu = np.ascontiguousarray(prob.mu, dtype=np.float64)
         f = np.ascontiguousarray(prob.forcing, dtype=np.float64) if forcing else None
         s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
-        self.ctx = L.ewh_create(desc, rho, lam, mu, prob.omega, f, prob.nrhs, s)
+        mapping = getattr(prob, "mapping", None)
+        if mapping is not None:  # curvilinear grid: node coordinates (x, y)
+            X = np.ascontiguousarray(mapping[0], dtype=np.float64)
+            Y = np.ascontiguousarray(mapping[1], dtype=np.float64)
+            self.ctx = L.ewh_create_mapped(desc, X, Y, rho, lam, mu, prob.omega, f, prob.nrhs, s)
+        else:
+            self.ctx = L.ewh_create(desc, rho, lam, mu, prob.omega, f, prob.nrhs, s)
         self.info = L.ewh_get_info(self.ctx)
         self.nrhs = prob.nrhs
         self.n = int(self.info.n_unknowns) * prob.nrhs
@@ -146,6 +152,8 @@ class WaveHoltzBatch:
         self._keep = []
         items = []
         for p in self.probs:
+            if getattr(p, "mapping", None) is not None:
+                raise ValueError("batch members must be Cartesian grids (mapped grids run as WaveHoltz contexts)")
             desc = make_desc(p.dim, p.n, p.h, p.order, p.bc, PRECISIONS[precision], p.cfl, p.periods,
                              p.corrected, 0, getattr(p, "implicit", 0))
             arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (p.rho, p.lam, p.mu, p.forcing)]

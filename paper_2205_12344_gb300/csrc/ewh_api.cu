@@ -34,7 +34,8 @@ struct Wave {
   T* mu = nullptr;
   T* irh2 = nullptr;
   T* frho = nullptr;   // null when the problem has no forcing
-  T* sigma = nullptr;  // order 4 only
+  T* sigma = nullptr;  // order 4 only (mapped grids: the four fluxes)
+  T* met = nullptr;    // mapped grids: metric planes (y_r, -x_r, -y_q, x_q, 1/J)
   cudaGraphExec_t graph_S = nullptr;
   cudaGraphExec_t graph_Pi0 = nullptr;
   long long graph_S_kernels = 0;
@@ -134,10 +135,11 @@ ewh_status fail(ewh_ctx* ctx, ewh_status s, const std::string& msg) {
 long long total_unknowns(const ewh_ctx* c) { return (long long)c->g.nrhs * c->g.dim * c->g.nodes; }
 
 template <typename T>
-cudaError_t alloc_zero(T** p, size_t count) {
+cudaError_t alloc_zero(T** p, size_t count, cudaStream_t st) {
   cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
   if (e != cudaSuccess) return e;
-  return cudaMemset(*p, 0, count * sizeof(T));
+  // zeroed on the context's (non-blocking) stream, ahead of the kernels that fill it
+  return cudaMemsetAsync(*p, 0, count * sizeof(T), st);
 }
 
 // full-grid FP64 -> padded T (one component), optionally scaled by 1/rho
@@ -160,27 +162,33 @@ __global__ void to_padded_kernel(Geom g, const double* __restrict__ src, const d
 
 template <typename T>
 ewh_status build_wave(ewh_ctx* ctx, Wave<T>& w, const double* d_rho, const double* d_lam, const double* d_mu,
-                      const double* d_f) {
+                      const double* d_f, const double* d_met) {
   const Geom& g = ctx->g;
   const size_t field = (size_t)g.field;
   const size_t state = field * g.dim * g.nrhs;
-  EWH_CU(alloc_zero(&w.u_a, state));
-  EWH_CU(alloc_zero(&w.u_b, state));
-  EWH_CU(alloc_zero(&w.delta, state));
-  EWH_CU(alloc_zero(&w.acc, state));
-  EWH_CU(alloc_zero(&w.lam, field));
-  EWH_CU(alloc_zero(&w.mu, field));
-  EWH_CU(alloc_zero(&w.irh2, field));
-  if (ctx->order == 4) EWH_CU(alloc_zero(&w.sigma, field * (g.dim == 2 ? 3 : 6) * g.nrhs));
+  EWH_CU(alloc_zero(&w.u_a, state, ctx->st));
+  EWH_CU(alloc_zero(&w.u_b, state, ctx->st));
+  EWH_CU(alloc_zero(&w.delta, state, ctx->st));
+  EWH_CU(alloc_zero(&w.acc, state, ctx->st));
+  EWH_CU(alloc_zero(&w.lam, field, ctx->st));
+  EWH_CU(alloc_zero(&w.mu, field, ctx->st));
+  EWH_CU(alloc_zero(&w.irh2, field, ctx->st));
+  if (ctx->order == 4) EWH_CU(alloc_zero(&w.sigma, field * (g.mapped ? 4 : (g.dim == 2 ? 3 : 6)) * g.nrhs, ctx->st));
   const long long full = (long long)g.n[0] * g.n[1] * g.n[2];
   const int blocks = (int)std::min<long long>((full + 255) / 256, 4096);
   const double h2 = ctx->h * ctx->h;
+  if (g.mapped) {
+    EWH_CU(alloc_zero(&w.met, field * 5, ctx->st));
+    for (int k = 0; k < 5; ++k)
+      to_padded_kernel<T><<<blocks, 256, 0, ctx->st>>>(g, d_met + (size_t)k * full, d_rho, 0, h2, w.met + k * field);
+    ctx->launches += 5;
+  }
   to_padded_kernel<T><<<blocks, 256, 0, ctx->st>>>(g, d_lam, d_rho, 0, h2, w.lam);
   to_padded_kernel<T><<<blocks, 256, 0, ctx->st>>>(g, d_mu, d_rho, 0, h2, w.mu);
   to_padded_kernel<T><<<blocks, 256, 0, ctx->st>>>(g, d_rho, d_rho, 1, h2, w.irh2);
   ctx->launches += 3;
   if (d_f) {
-    EWH_CU(alloc_zero(&w.frho, state));
+    EWH_CU(alloc_zero(&w.frho, state, ctx->st));
     for (int r = 0; r < g.nrhs; ++r)
       for (int c = 0; c < g.dim; ++c) {
         to_padded_kernel<T><<<blocks, 256, 0, ctx->st>>>(g, d_f + (size_t)(r * g.dim + c) * full, d_rho, 2, h2,
@@ -189,7 +197,7 @@ ewh_status build_wave(ewh_ctx* ctx, Wave<T>& w, const double* d_rho, const doubl
       }
   }
   EWH_CU(cudaGetLastError());
-  if (sizeof(T) == 4 && g.dim == 2 && ctx->order == 4 && g.nrhs == 1) {
+  if (sizeof(T) == 4 && g.dim == 2 && ctx->order == 4 && g.nrhs == 1 && !g.mapped) {
     const int N = ctx->nt * ctx->periods;
     std::vector<double> hc(N), hw(N);
     for (int n = 0; n < N; ++n) {  // the same values as the per-level launches get
@@ -198,7 +206,7 @@ ewh_status build_wave(ewh_ctx* ctx, Wave<T>& w, const double* d_rho, const doubl
     }
     EWH_CU(cudaMalloc(&w.d_cosn, sizeof(double) * N));
     EWH_CU(cudaMalloc(&w.d_wnew, sizeof(double) * N));
-    EWH_CU(alloc_zero(&w.bar, 2));
+    EWH_CU(alloc_zero(&w.bar, 2, ctx->st));
     EWH_CU(cudaMemcpy(w.d_cosn, hc.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
     EWH_CU(cudaMemcpy(w.d_wnew, hw.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
     for (int k = 0; k < RS_SHAPES; ++k) w.rplan[k] = plan_resident_o4(g, k);
@@ -219,6 +227,7 @@ void free_wave(Wave<T>& w) {
   cudaFree(w.irh2);
   cudaFree(w.frho);
   cudaFree(w.sigma);
+  cudaFree(w.met);
   cudaFree(w.d_cosn);
   cudaFree(w.d_wnew);
   cudaFree(w.bar);
@@ -366,7 +375,7 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
     }
   }
   const char* off = getenv("EWH_AUTOTUNE");
-  if (nv <= 1 || (off && off[0] == '0')) {
+  if (nv <= 1 || ctx->g.mapped || (off && off[0] == '0')) {  // mapped grids: one launcher
     w.variant = 0;
     return;
   }
@@ -389,6 +398,7 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
   f.irh2 = w.irh2;
   f.frho = nullptr;
   f.sigma = w.sigma;
+  f.met = w.met;
   StepScalars sc{ctx->kt, 1.0, 0.0, 0.0};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -474,6 +484,7 @@ cudaError_t enqueue_steps(ewh_ctx* ctx, Wave<T>& w, bool forced, long long* nl) 
   f.irh2 = w.irh2;
   f.frho = forced ? w.frho : nullptr;
   f.sigma = w.sigma;
+  f.met = w.met;
   f.delta = w.delta;
   f.acc = w.acc;
   const double two_pi = 2.0 * M_PI;
@@ -615,7 +626,7 @@ ewh_status implicit_minvK(ewh_ctx* ctx, const double* src, double* dst) {
   Wave<double>& w = ctx->w64;
   EWH_CU(launch_pack<double>(ctx->g, src, w.u_a, ctx->st));
   EWH_CU(launch_minvK<double>(ctx->g, ctx->order, w.u_a, w.u_b, w.lam, w.mu, w.irh2, w.sigma, ctx->st,
-                              &ctx->launches));
+                              &ctx->launches, w.met));
   EWH_CU(launch_unpack<double>(ctx->g, w.u_b, dst, nullptr, ctx->st));
   ctx->launches += 2;
   return EWH_OK;
@@ -1485,6 +1496,276 @@ ewh_status batch_solve_T(ewh_batch* b, double tol, int maxit, double* const* v_o
 // ===========================================================================
 // C ABI
 // ===========================================================================
+namespace {
+
+// Context creation; xmap/ymap (node coordinates of a mapped 2D grid) may be null.
+ewh_status create_impl(const ewh_grid_desc* desc, const double* xmap, const double* ymap, const double* rho,
+                       const double* lambda, const double* mu, double omega, const double* forcing, int nrhs,
+                       void* cuda_stream, ewh_ctx** out) {
+  if (!out) return fail(nullptr, EWH_EINVAL, "out is NULL");
+  *out = nullptr;
+  ewh_status vs = validate_desc(desc, nrhs);
+  if (vs != EWH_OK) return vs;
+  if (!rho || !lambda || !mu) return fail(nullptr, EWH_EINVAL, "rho, lambda and mu are required");
+  if (!(omega > 0.0) || !std::isfinite(omega)) return fail(nullptr, EWH_EINVAL, "omega must be positive and finite");
+  const int dim = desc->dim;
+  const long long full = (long long)desc->n[0] * desc->n[1] * (dim == 3 ? desc->n[2] : 1);
+  // media on the host for validation and the time-step bound
+  std::vector<double> hr(full), hl(full), hm(full);
+  auto fetch = [&](const double* src, std::vector<double>& dst) -> cudaError_t {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, src) == cudaSuccess &&
+        (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged))
+      return cudaMemcpy(dst.data(), src, sizeof(double) * full, cudaMemcpyDeviceToHost);
+    cudaGetLastError();  // host memory (or no device): plain copy
+    std::memcpy(dst.data(), src, sizeof(double) * full);
+    return cudaSuccess;
+  };
+  if (fetch(rho, hr) != cudaSuccess || fetch(lambda, hl) != cudaSuccess || fetch(mu, hm) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, EWH_EINVAL, "cannot read rho/lambda/mu");
+  }
+  const bool mapped = xmap != nullptr;
+  std::vector<double> hmet;  // mapped grids: (y_r, -x_r, -y_q, x_q, 1/J, J) per node
+  double* d_met = nullptr;
+  if (mapped) {  // Section 4.1, curvilinear form: metric terms from the SBP derivative of the mapping
+    if (dim != 2 || desc->order != 4)
+      return fail(nullptr, EWH_EINVAL, "mapped grids need dim 2 and order 4");
+    std::vector<double> hx(full), hy(full);
+    if (fetch(xmap, hx) != cudaSuccess || fetch(ymap, hy) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(nullptr, EWH_EINVAL, "cannot read the node coordinates");
+    }
+    for (long long i = 0; i < full; ++i)
+      if (!std::isfinite(hx[i]) || !std::isfinite(hy[i]))
+        return fail(nullptr, EWH_EINVAL, "node coordinates must be finite");
+    hmet.resize(6 * full);
+    double *d_xy = nullptr;
+    cudaStream_t ts = nullptr;
+    bool ok = cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaMalloc(&d_xy, sizeof(double) * 2 * full) == cudaSuccess &&
+              cudaMalloc(&d_met, sizeof(double) * 6 * full) == cudaSuccess &&
+              cudaMemcpyAsync(d_xy, hx.data(), sizeof(double) * full, cudaMemcpyHostToDevice, ts) == cudaSuccess &&
+              cudaMemcpyAsync(d_xy + full, hy.data(), sizeof(double) * full, cudaMemcpyHostToDevice, ts) == cudaSuccess &&
+              launch_curv_metrics(desc->n[0], desc->n[1], desc->h, d_xy, d_xy + full, d_met, ts) == cudaSuccess &&
+              cudaMemcpyAsync(hmet.data(), d_met, sizeof(double) * 6 * full, cudaMemcpyDeviceToHost, ts) == cudaSuccess &&
+              cudaStreamSynchronize(ts) == cudaSuccess;
+    cudaFree(d_xy);
+    if (ts) cudaStreamDestroy(ts);
+    if (!ok) {
+      cudaGetLastError();
+      cudaFree(d_met);
+      return fail(nullptr, EWH_ECUDA, "metric computation failed (no CUDA device?)");
+    }
+    for (long long i = 0; i < full; ++i)
+      if (!(hmet[5 * full + i] > 0.0) || !std::isfinite(hmet[5 * full + i])) {
+        cudaFree(d_met);
+        return fail(nullptr, EWH_EINVAL, "mapping not orientation preserving at node " + std::to_string(i) + " (J <= 0)");
+      }
+  }
+  double speed2 = 0.0;
+  for (long long i = 0; i < full; ++i) {
+    const double r = hr[i], l = hl[i], m = hm[i];
+    if (!std::isfinite(r) || !std::isfinite(l) || !std::isfinite(m) || !(r > 0.0) || !(m > 0.0) ||
+        !(l > -2.0 * m / dim)) {
+      cudaFree(d_met);
+      return fail(nullptr, EWH_EINVAL,
+                  "invalid medium at node " + std::to_string(i) + ": need finite rho > 0, mu > 0, lambda > -2 mu / dim");
+    }
+    double c2 = (l + (dim + 1) * m) / r;
+    if (mapped) {  // (|grad q|^2 + |grad r|^2) / 2 scales the Cartesian bound
+      const double a0 = hmet[i], a1 = hmet[full + i], a2 = hmet[2 * full + i], a3 = hmet[3 * full + i];
+      const double iJ = hmet[4 * full + i];
+      c2 *= 0.5 * (a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3) * iJ * iJ;
+    }
+    if (c2 > speed2) speed2 = c2;
+  }
+  std::vector<double> hf;  // mapped grids: J f, so that (J f) / (rho J) = f / rho
+  if (mapped) {
+    for (long long i = 0; i < full; ++i) hr[i] *= hmet[5 * full + i];  // the mass density rho J
+    if (forcing) {
+      hf.resize((size_t)full * dim * nrhs);
+      cudaPointerAttributes at;
+      if (cudaPointerGetAttributes(&at, forcing) == cudaSuccess &&
+          (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
+        if (cudaMemcpy(hf.data(), forcing, sizeof(double) * hf.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+          cudaGetLastError();
+          cudaFree(d_met);
+          return fail(nullptr, EWH_EINVAL, "cannot read the forcing");
+        }
+      } else {
+        cudaGetLastError();
+        std::memcpy(hf.data(), forcing, sizeof(double) * hf.size());
+      }
+      for (size_t k = 0; k < hf.size(); ++k) hf[k] *= hmet[5 * full + (long long)(k % full)];
+      forcing = hf.data();
+    }
+  }
+
+  ewh_ctx* ctx = new ewh_ctx();
+  ctx->order = desc->order;
+  ctx->precision = desc->precision;
+  ctx->periods = desc->periods;
+  ctx->corrected = desc->corrected ? 1 : 0;
+  ctx->h = desc->h;
+  ctx->omega = omega;
+  ctx->user_stream = (cudaStream_t)cuda_stream;
+  Geom& g = ctx->g;
+  g.dim = dim;
+  g.nrhs = nrhs;
+  g.mapped = mapped ? 1 : 0;
+  for (int a = 0; a < 3; ++a) {
+    g.n[a] = a < dim ? desc->n[a] : 1;
+    g.lo_free[a] = a < dim ? (desc->bc[2 * a] == EWH_BC_FREE) : 1;
+    g.hi_free[a] = a < dim ? (desc->bc[2 * a + 1] == EWH_BC_FREE) : 1;
+  }
+  for (int a = 0; a < 3; ++a) {
+    if (a < dim) {
+      const int rounded = ((g.n[a] + TILE_ROUND - 1) / TILE_ROUND) * TILE_ROUND;
+      g.np[a] = rounded + 2 * PAD;
+      g.off[a] = g.lo_free[a] ? 0 : 1;
+      g.nu[a] = g.n[a] - (g.lo_free[a] ? 0 : 1) - (g.hi_free[a] ? 0 : 1);
+    } else {
+      g.np[a] = 1;
+      g.off[a] = 0;
+      g.nu[a] = 1;
+    }
+  }
+  g.pz = dim == 3 ? PAD : 0;
+  g.plane = (long long)g.np[0] * g.np[1];
+  g.field = g.plane * g.np[2];
+  g.nodes = (long long)g.nu[0] * g.nu[1] * g.nu[2];
+
+  // time step (Section 4.3): dt_CFL, nt, dt, w~, c, kt and trapezoid weights
+  const double cfl = desc->cfl == 0.0 ? 0.5 : desc->cfl;
+  const double T = 2.0 * M_PI / omega;
+  const double dtc = cfl * desc->h / std::sqrt(speed2);
+  int nt = desc->nt;
+  if (nt == 0) {
+    const double q = std::ceil(T / dtc);
+    if (q > 1e7) {
+      cudaFree(d_met);
+      delete ctx;
+      return fail(nullptr, EWH_EINVAL, "more than 1e7 time steps per period");
+    }
+    nt = std::max(5, (int)q);
+  }
+  ctx->nt = nt;
+  ctx->dt = T / nt;
+  ctx->omega_t = 2.0 * std::sin(omega * ctx->dt / 2.0) / ctx->dt;
+  ctx->c = ctx->corrected ? (ctx->omega_t / omega) * (ctx->omega_t / omega) : 1.0;
+  ctx->kt = ctx->c * ctx->dt * ctx->dt;
+  const int N = nt * ctx->periods;
+  ctx->weights.resize(N + 1);
+  for (int k = 0; k <= N; ++k) {
+    const double eta = (k == 0 || k == N) ? 0.5 : 1.0;
+    ctx->weights[k] = (2.0 / N) * eta * (std::cos(2.0 * M_PI * k / nt) - 0.25);
+  }
+  ctx->has_forcing = forcing != nullptr;
+  if (desc->implicit) {  // Section 4.4: alpha (eq. alpha), or 2 for the unmodified scheme
+    const double wd = omega * ctx->dt;
+    ctx->implicit = 1;
+    ctx->alpha = ctx->corrected ? std::cos(wd) * (2.0 + wd * wd) : 2.0;
+    ctx->omega_t = std::cos(wd) > 0.0 ? 2.0 * std::sin(wd / 2.0) / (ctx->dt * std::sqrt(std::cos(wd))) : NAN;
+    ctx->kt = 0.0;
+    if (!(std::fabs(ctx->alpha) < 2.0) && ctx->corrected) {
+      cudaFree(d_met);
+      delete ctx;
+      return fail(nullptr, EWH_EINVAL, "implicit scheme unstable: |alpha| >= 2 (use nt >= 5)");
+    }
+  }
+
+  // CUDA resources
+  auto bail = [&](ewh_status s, const std::string& m) {
+    g_create_error = m;
+    cudaFree(d_met);
+    ewh_destroy(ctx);
+    return s;
+  };
+  if (cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(EWH_ECUDA, "cannot create stream/events (no CUDA device?)");
+  }
+  enter(ctx);
+  double *d_r = nullptr, *d_l = nullptr, *d_m = nullptr, *d_f = nullptr;
+  const size_t fbytes = sizeof(double) * (size_t)full * dim * nrhs;
+  bool ok = cudaMalloc(&d_r, sizeof(double) * full) == cudaSuccess &&
+            cudaMalloc(&d_l, sizeof(double) * full) == cudaSuccess &&
+            cudaMalloc(&d_m, sizeof(double) * full) == cudaSuccess &&
+            (!forcing || cudaMalloc(&d_f, fbytes) == cudaSuccess);
+  if (!ok) {
+    cudaGetLastError();
+    cudaFree(d_r);
+    cudaFree(d_l);
+    cudaFree(d_m);
+    cudaFree(d_f);
+    return bail(EWH_ENOMEM, "device allocation of the medium failed");
+  }
+  cudaMemcpyAsync(d_r, hr.data(), sizeof(double) * full, cudaMemcpyHostToDevice, ctx->st);
+  cudaMemcpyAsync(d_l, hl.data(), sizeof(double) * full, cudaMemcpyHostToDevice, ctx->st);
+  cudaMemcpyAsync(d_m, hm.data(), sizeof(double) * full, cudaMemcpyHostToDevice, ctx->st);
+  if (forcing) cudaMemcpyAsync(d_f, forcing, fbytes, cudaMemcpyDefault, ctx->st);
+
+  ewh_status s = build_wave<double>(ctx, ctx->w64, d_r, d_l, d_m, d_f, d_met);
+  if (s == EWH_OK && ctx->precision == EWH_FP32_STENCIL)
+    s = build_wave<float>(ctx, ctx->w32, d_r, d_l, d_m, d_f, d_met);
+  const long long n = total_unknowns(ctx);
+  ctx->nblk = dot_blocks(g);
+  if (s == EWH_OK) {
+    ok = alloc_zero(&ctx->kx, n, ctx->st) == cudaSuccess && alloc_zero(&ctx->kr, n, ctx->st) == cudaSuccess &&
+         alloc_zero(&ctx->kp, n, ctx->st) == cudaSuccess && alloc_zero(&ctx->kq, n, ctx->st) == cudaSuccess &&
+         alloc_zero(&ctx->kb, n, ctx->st) == cudaSuccess && alloc_zero(&ctx->kd, n, ctx->st) == cudaSuccess &&
+         alloc_zero(&ctx->ktmp, n, ctx->st) == cudaSuccess && alloc_zero(&ctx->mw, g.nodes, ctx->st) == cudaSuccess &&
+         alloc_zero(&ctx->kar, n, ctx->st) == cudaSuccess && alloc_zero(&ctx->kap, n, ctx->st) == cudaSuccess &&
+         alloc_zero(&ctx->part, (size_t)ctx->nblk * nrhs, ctx->st) == cudaSuccess &&
+         alloc_zero(&ctx->scal, (size_t)S_N * nrhs, ctx->st) == cudaSuccess &&
+         alloc_zero(&ctx->active, nrhs, ctx->st) == cudaSuccess && alloc_zero(&ctx->flags, 1, ctx->st) == cudaSuccess &&
+         cudaMallocHost(&ctx->h_scal, sizeof(double) * S_N * nrhs) == cudaSuccess &&
+         cudaMallocHost(&ctx->h_act, sizeof(int) * nrhs) == cudaSuccess &&
+         cudaMallocHost(&ctx->h_flag, sizeof(int)) == cudaSuccess;
+    if (ok && ctx->implicit) {
+      for (double** q : {&ctx->iu_prev, &ctx->iu, &ctx->iu_next, &ctx->ig, &ctx->ir, &ctx->ip, &ctx->iq, &ctx->iacc})
+        ok = ok && alloc_zero(q, n, ctx->st) == cudaSuccess;
+      ok = ok && alloc_zero(&ctx->iscal, (size_t)I_N * nrhs, ctx->st) == cudaSuccess;
+      if (ok && forcing) ok = alloc_zero(&ctx->ifr, n, ctx->st) == cudaSuccess;
+    }
+    if (!ok) {
+      cudaGetLastError();
+      s = fail(ctx, EWH_ENOMEM, "device allocation of the Krylov workspace failed");
+    }
+  }
+  if (s == EWH_OK && ctx->ifr) {  // f / rho at the unknowns, dense (from the padded FP64 field)
+    if (launch_unpack<double>(g, ctx->w64.frho, ctx->ifr, nullptr, ctx->st) != cudaSuccess)
+      s = fail(ctx, EWH_ECUDA, "forcing unpack failed");
+    ctx->launches += 1;
+  }
+  if (s == EWH_OK) {
+    if (launch_fill_mass(g, ctx->order, d_r, desc->h, ctx->mw, ctx->st) != cudaSuccess)
+      s = fail(ctx, EWH_ECUDA, "mass kernel launch failed");
+    ctx->launches += 1;
+  }
+  cudaError_t e = cudaStreamSynchronize(ctx->st);
+  cudaFree(d_met);
+  d_met = nullptr;
+  cudaFree(d_r);
+  cudaFree(d_l);
+  cudaFree(d_m);
+  cudaFree(d_f);
+  if (s == EWH_OK && e != cudaSuccess) s = fail(ctx, EWH_ECUDA, std::string("setup: ") + cudaGetErrorString(e));
+  if (s != EWH_OK) {
+    std::string m = ctx->err;
+    if (m == "no error") m = g_create_error;
+    return bail(s, m);
+  }
+  leave(ctx);
+  *out = ctx;
+  return EWH_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* ewh_status_string(int s) {
@@ -1540,193 +1821,15 @@ void ewh_destroy(ewh_ctx* ctx) {
 
 ewh_status ewh_create(const ewh_grid_desc* desc, const double* rho, const double* lambda, const double* mu,
                       double omega, const double* forcing, int nrhs, void* cuda_stream, ewh_ctx** out) {
-  if (!out) return fail(nullptr, EWH_EINVAL, "out is NULL");
-  *out = nullptr;
-  ewh_status vs = validate_desc(desc, nrhs);
-  if (vs != EWH_OK) return vs;
-  if (!rho || !lambda || !mu) return fail(nullptr, EWH_EINVAL, "rho, lambda and mu are required");
-  if (!(omega > 0.0) || !std::isfinite(omega)) return fail(nullptr, EWH_EINVAL, "omega must be positive and finite");
-  const int dim = desc->dim;
-  const long long full = (long long)desc->n[0] * desc->n[1] * (dim == 3 ? desc->n[2] : 1);
-  // media on the host for validation and the time-step bound
-  std::vector<double> hr(full), hl(full), hm(full);
-  auto fetch = [&](const double* src, std::vector<double>& dst) -> cudaError_t {
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, src) == cudaSuccess &&
-        (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged))
-      return cudaMemcpy(dst.data(), src, sizeof(double) * full, cudaMemcpyDeviceToHost);
-    cudaGetLastError();  // host memory (or no device): plain copy
-    std::memcpy(dst.data(), src, sizeof(double) * full);
-    return cudaSuccess;
-  };
-  if (fetch(rho, hr) != cudaSuccess || fetch(lambda, hl) != cudaSuccess || fetch(mu, hm) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(nullptr, EWH_EINVAL, "cannot read rho/lambda/mu");
-  }
-  double speed2 = 0.0;
-  for (long long i = 0; i < full; ++i) {
-    const double r = hr[i], l = hl[i], m = hm[i];
-    if (!std::isfinite(r) || !std::isfinite(l) || !std::isfinite(m) || !(r > 0.0) || !(m > 0.0) ||
-        !(l > -2.0 * m / dim))
-      return fail(nullptr, EWH_EINVAL,
-                  "invalid medium at node " + std::to_string(i) + ": need finite rho > 0, mu > 0, lambda > -2 mu / dim");
-    const double c2 = (l + (dim + 1) * m) / r;
-    if (c2 > speed2) speed2 = c2;
-  }
+  return create_impl(desc, nullptr, nullptr, rho, lambda, mu, omega, forcing, nrhs, cuda_stream, out);
+}
 
-  ewh_ctx* ctx = new ewh_ctx();
-  ctx->order = desc->order;
-  ctx->precision = desc->precision;
-  ctx->periods = desc->periods;
-  ctx->corrected = desc->corrected ? 1 : 0;
-  ctx->h = desc->h;
-  ctx->omega = omega;
-  ctx->user_stream = (cudaStream_t)cuda_stream;
-  Geom& g = ctx->g;
-  g.dim = dim;
-  g.nrhs = nrhs;
-  for (int a = 0; a < 3; ++a) {
-    g.n[a] = a < dim ? desc->n[a] : 1;
-    g.lo_free[a] = a < dim ? (desc->bc[2 * a] == EWH_BC_FREE) : 1;
-    g.hi_free[a] = a < dim ? (desc->bc[2 * a + 1] == EWH_BC_FREE) : 1;
-  }
-  for (int a = 0; a < 3; ++a) {
-    if (a < dim) {
-      const int rounded = ((g.n[a] + TILE_ROUND - 1) / TILE_ROUND) * TILE_ROUND;
-      g.np[a] = rounded + 2 * PAD;
-      g.off[a] = g.lo_free[a] ? 0 : 1;
-      g.nu[a] = g.n[a] - (g.lo_free[a] ? 0 : 1) - (g.hi_free[a] ? 0 : 1);
-    } else {
-      g.np[a] = 1;
-      g.off[a] = 0;
-      g.nu[a] = 1;
-    }
-  }
-  g.pz = dim == 3 ? PAD : 0;
-  g.plane = (long long)g.np[0] * g.np[1];
-  g.field = g.plane * g.np[2];
-  g.nodes = (long long)g.nu[0] * g.nu[1] * g.nu[2];
-
-  // time step (Section 4.3): dt_CFL, nt, dt, w~, c, kt and trapezoid weights
-  const double cfl = desc->cfl == 0.0 ? 0.5 : desc->cfl;
-  const double T = 2.0 * M_PI / omega;
-  const double dtc = cfl * desc->h / std::sqrt(speed2);
-  int nt = desc->nt;
-  if (nt == 0) {
-    const double q = std::ceil(T / dtc);
-    if (q > 1e7) {
-      delete ctx;
-      return fail(nullptr, EWH_EINVAL, "more than 1e7 time steps per period");
-    }
-    nt = std::max(5, (int)q);
-  }
-  ctx->nt = nt;
-  ctx->dt = T / nt;
-  ctx->omega_t = 2.0 * std::sin(omega * ctx->dt / 2.0) / ctx->dt;
-  ctx->c = ctx->corrected ? (ctx->omega_t / omega) * (ctx->omega_t / omega) : 1.0;
-  ctx->kt = ctx->c * ctx->dt * ctx->dt;
-  const int N = nt * ctx->periods;
-  ctx->weights.resize(N + 1);
-  for (int k = 0; k <= N; ++k) {
-    const double eta = (k == 0 || k == N) ? 0.5 : 1.0;
-    ctx->weights[k] = (2.0 / N) * eta * (std::cos(2.0 * M_PI * k / nt) - 0.25);
-  }
-  ctx->has_forcing = forcing != nullptr;
-  if (desc->implicit) {  // Section 4.4: alpha (eq. alpha), or 2 for the unmodified scheme
-    const double wd = omega * ctx->dt;
-    ctx->implicit = 1;
-    ctx->alpha = ctx->corrected ? std::cos(wd) * (2.0 + wd * wd) : 2.0;
-    ctx->omega_t = std::cos(wd) > 0.0 ? 2.0 * std::sin(wd / 2.0) / (ctx->dt * std::sqrt(std::cos(wd))) : NAN;
-    ctx->kt = 0.0;
-    if (!(std::fabs(ctx->alpha) < 2.0) && ctx->corrected) {
-      delete ctx;
-      return fail(nullptr, EWH_EINVAL, "implicit scheme unstable: |alpha| >= 2 (use nt >= 5)");
-    }
-  }
-
-  // CUDA resources
-  auto bail = [&](ewh_status s, const std::string& m) {
-    g_create_error = m;
-    ewh_destroy(ctx);
-    return s;
-  };
-  if (cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess) {
-    cudaGetLastError();
-    return bail(EWH_ECUDA, "cannot create stream/events (no CUDA device?)");
-  }
-  enter(ctx);
-  double *d_r = nullptr, *d_l = nullptr, *d_m = nullptr, *d_f = nullptr;
-  const size_t fbytes = sizeof(double) * (size_t)full * dim * nrhs;
-  bool ok = cudaMalloc(&d_r, sizeof(double) * full) == cudaSuccess &&
-            cudaMalloc(&d_l, sizeof(double) * full) == cudaSuccess &&
-            cudaMalloc(&d_m, sizeof(double) * full) == cudaSuccess &&
-            (!forcing || cudaMalloc(&d_f, fbytes) == cudaSuccess);
-  if (!ok) {
-    cudaGetLastError();
-    cudaFree(d_r);
-    cudaFree(d_l);
-    cudaFree(d_m);
-    cudaFree(d_f);
-    return bail(EWH_ENOMEM, "device allocation of the medium failed");
-  }
-  cudaMemcpyAsync(d_r, hr.data(), sizeof(double) * full, cudaMemcpyHostToDevice, ctx->st);
-  cudaMemcpyAsync(d_l, hl.data(), sizeof(double) * full, cudaMemcpyHostToDevice, ctx->st);
-  cudaMemcpyAsync(d_m, hm.data(), sizeof(double) * full, cudaMemcpyHostToDevice, ctx->st);
-  if (forcing) cudaMemcpyAsync(d_f, forcing, fbytes, cudaMemcpyDefault, ctx->st);
-
-  ewh_status s = build_wave<double>(ctx, ctx->w64, d_r, d_l, d_m, d_f);
-  if (s == EWH_OK && ctx->precision == EWH_FP32_STENCIL) s = build_wave<float>(ctx, ctx->w32, d_r, d_l, d_m, d_f);
-  const long long n = total_unknowns(ctx);
-  ctx->nblk = dot_blocks(g);
-  if (s == EWH_OK) {
-    ok = alloc_zero(&ctx->kx, n) == cudaSuccess && alloc_zero(&ctx->kr, n) == cudaSuccess &&
-         alloc_zero(&ctx->kp, n) == cudaSuccess && alloc_zero(&ctx->kq, n) == cudaSuccess &&
-         alloc_zero(&ctx->kb, n) == cudaSuccess && alloc_zero(&ctx->kd, n) == cudaSuccess &&
-         alloc_zero(&ctx->ktmp, n) == cudaSuccess && alloc_zero(&ctx->mw, g.nodes) == cudaSuccess &&
-         alloc_zero(&ctx->kar, n) == cudaSuccess && alloc_zero(&ctx->kap, n) == cudaSuccess &&
-         alloc_zero(&ctx->part, (size_t)ctx->nblk * nrhs) == cudaSuccess &&
-         alloc_zero(&ctx->scal, (size_t)S_N * nrhs) == cudaSuccess &&
-         alloc_zero(&ctx->active, nrhs) == cudaSuccess && alloc_zero(&ctx->flags, 1) == cudaSuccess &&
-         cudaMallocHost(&ctx->h_scal, sizeof(double) * S_N * nrhs) == cudaSuccess &&
-         cudaMallocHost(&ctx->h_act, sizeof(int) * nrhs) == cudaSuccess &&
-         cudaMallocHost(&ctx->h_flag, sizeof(int)) == cudaSuccess;
-    if (ok && ctx->implicit) {
-      for (double** q : {&ctx->iu_prev, &ctx->iu, &ctx->iu_next, &ctx->ig, &ctx->ir, &ctx->ip, &ctx->iq, &ctx->iacc})
-        ok = ok && alloc_zero(q, n) == cudaSuccess;
-      ok = ok && alloc_zero(&ctx->iscal, (size_t)I_N * nrhs) == cudaSuccess;
-      if (ok && forcing) ok = alloc_zero(&ctx->ifr, n) == cudaSuccess;
-    }
-    if (!ok) {
-      cudaGetLastError();
-      s = fail(ctx, EWH_ENOMEM, "device allocation of the Krylov workspace failed");
-    }
-  }
-  if (s == EWH_OK && ctx->ifr) {  // f / rho at the unknowns, dense (from the padded FP64 field)
-    if (launch_unpack<double>(g, ctx->w64.frho, ctx->ifr, nullptr, ctx->st) != cudaSuccess)
-      s = fail(ctx, EWH_ECUDA, "forcing unpack failed");
-    ctx->launches += 1;
-  }
-  if (s == EWH_OK) {
-    if (launch_fill_mass(g, ctx->order, d_r, desc->h, ctx->mw, ctx->st) != cudaSuccess)
-      s = fail(ctx, EWH_ECUDA, "mass kernel launch failed");
-    ctx->launches += 1;
-  }
-  cudaError_t e = cudaStreamSynchronize(ctx->st);
-  cudaFree(d_r);
-  cudaFree(d_l);
-  cudaFree(d_m);
-  cudaFree(d_f);
-  if (s == EWH_OK && e != cudaSuccess) s = fail(ctx, EWH_ECUDA, std::string("setup: ") + cudaGetErrorString(e));
-  if (s != EWH_OK) {
-    std::string m = ctx->err;
-    if (m == "no error") m = g_create_error;
-    return bail(s, m);
-  }
-  leave(ctx);
-  *out = ctx;
-  return EWH_OK;
+ewh_status ewh_create_mapped(const ewh_grid_desc* desc, const double* x, const double* y, const double* rho,
+                             const double* lambda, const double* mu, double omega, const double* forcing, int nrhs,
+                             void* cuda_stream, ewh_ctx** out) {
+  if (out) *out = nullptr;
+  if (!x || !y) return fail(nullptr, EWH_EINVAL, "x and y (node coordinates) are required");
+  return create_impl(desc, x, y, rho, lambda, mu, omega, forcing, nrhs, cuda_stream, out);
 }
 
 ewh_status ewh_get_info(const ewh_ctx* ctx, ewh_problem_info* info) {
@@ -1799,7 +1902,7 @@ ewh_status ewh_apply_minvK(ewh_ctx* ctx, const double* u, double* out) {
   Wave<double>& w = ctx->w64;
   if (launch_pack<double>(ctx->g, u, w.u_a, ctx->st) != cudaSuccess ||
       launch_minvK<double>(ctx->g, ctx->order, w.u_a, w.u_b, w.lam, w.mu, w.irh2, w.sigma, ctx->st,
-                           &ctx->launches) != cudaSuccess ||
+                           &ctx->launches, w.met) != cudaSuccess ||
       launch_unpack<double>(ctx->g, w.u_b, out, nullptr, ctx->st) != cudaSuccess)
     s = fail(ctx, EWH_ECUDA, "operator launch failed");
   ctx->launches += 2;

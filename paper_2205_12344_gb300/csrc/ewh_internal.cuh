@@ -28,6 +28,7 @@ struct Geom {
   long long nodes; // unknown nodes per component
   int nrhs;
   int variant;     // step-kernel variant chosen by the autotuner (host side)
+  int mapped;      // 1: curvilinear 2D grid (order 4): fluxes through WaveFields::met
 };
 
 // Number of step-kernel variants worth timing for a geometry/order.
@@ -78,6 +79,7 @@ struct WaveFields {
   const T* irh2;   // 1 / (rho h^2)
   const T* frho;   // f / rho per rhs and component, or nullptr (S apply)
   T* sigma;        // order-4 stress scratch (dim*(dim+1)/2 fields per rhs) or nullptr
+  const T* met = nullptr;  // mapped grids: 5 planes (y_r, -x_r, -y_q, x_q, 1/J) of one padded component
 };
 
 // ---- launchers (ewh_stencil.cu) -------------------------------------------
@@ -86,7 +88,8 @@ cudaError_t launch_step(const Geom& g, int order, const WaveFields<T>& f, StepMo
                         const StepScalars& s, cudaStream_t st, long long* nlaunch);
 template <typename T>
 cudaError_t launch_minvK(const Geom& g, int order, const T* u, T* out, const T* lam,
-                         const T* mu, const T* irh2, T* sigma, cudaStream_t st, long long* nlaunch);
+                         const T* mu, const T* irh2, T* sigma, cudaStream_t st, long long* nlaunch,
+                         const T* met = nullptr);
 
 // ---- vector kernels (ewh_krylov.cu) -----------------------------------------
 // dense FP64 [rhs][comp][unknowns] <-> padded T
@@ -131,6 +134,9 @@ cudaError_t launch_cr_pupdate(const Geom& g, const double* r, const double* ar, 
 cudaError_t launch_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t st);
 cudaError_t launch_fill_mass(const Geom& g, int order, const double* rho_full, double h, double* mw,
                              cudaStream_t st);
+// mapped grids: 6 dense planes (y_r, -x_r, -y_q, x_q, 1/J, J) of n0*n1 nodes
+cudaError_t launch_curv_metrics(int n0, int n1, double h, const double* X, const double* Y, double* out,
+                                cudaStream_t st);
 
 // ---- on-chip resident wave solve (ewh_stencil.cu) --------------------------
 // Order 4 (SBP), 2D, FP32, one right-hand side: all nt*periods time levels in

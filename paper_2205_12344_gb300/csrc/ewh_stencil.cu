@@ -674,6 +674,115 @@ static int step2d_o4_tile(const Geom& g) {
   return (g.variant >= 0 && g.variant <= 3) ? g.variant : 0;
 }
 
+// ---------------------------------------------------------------------------
+// Order 4 (SBP), 2D, curvilinear grid (Section 4.1, curvilinear form): the
+// node grid is the image of (q, r) = (i h, j h) under a smooth mapping.  The
+// stress kernel forms physical derivatives from the SBP derivatives in q and
+// r, u_x = (y_r u_q - y_q u_r) / J, u_y = (x_q u_r - x_r u_q) / J, the
+// stresses, and the four J-weighted fluxes
+//   F^q_u = y_r s_xx - x_r s_xy,  F^r_u = -y_q s_xx + x_q s_xy,
+//   F^q_v = y_r s_xy - x_r s_yy,  F^r_v = -y_q s_xy + x_q s_yy;
+// the divergence kernel forms -D_q F^q - D_r F^r + H^{-1} B F (the Cartesian
+// kernel with the fluxes in place of the stresses) times 1/(rho J h^2).
+// One node per thread, global memory (the grid sizes of mapped problems are
+// moderate); the metric planes are (y_r, -x_r, -y_q, x_q, 1/J).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) curv_stress2d(Geom g, const T* __restrict__ u, const T* __restrict__ lam,
+                                                     const T* __restrict__ mu, const T* __restrict__ met,
+                                                     T* __restrict__ sig) {
+  if (g.dim != 2) return;
+  pdl_wait();
+  pdl_trigger();
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int rhs = blockIdx.z;
+  if (x >= g.n[0] || y >= g.n[1]) return;
+  const long long sy = g.np[0];
+  const long long pc = pidx(g, 0, 0, x, y, 0);
+  const T* U = u + pidx(g, rhs, 0, x, y, 0);
+  const T* V = U + g.field;
+  const T uq = sbp_d1<T>(U, 1, x, g.n[0]), ur = sbp_d1<T>(U, sy, y, g.n[1]);
+  const T vq = sbp_d1<T>(V, 1, x, g.n[0]), vr = sbp_d1<T>(V, sy, y, g.n[1]);
+  const T a0 = met[pc], a1 = met[g.field + pc], a2 = met[2 * g.field + pc], a3 = met[3 * g.field + pc];
+  const T ij = met[4 * g.field + pc];
+  const T u_x = (a0 * uq + a2 * ur) * ij, u_y = (a1 * uq + a3 * ur) * ij;
+  const T v_x = (a0 * vq + a2 * vr) * ij, v_y = (a1 * vq + a3 * vr) * ij;
+  const T l = lam[pc], m = mu[pc];
+  const T div = u_x + v_y;
+  const T sxx = l * div + T(2) * m * u_x, syy = l * div + T(2) * m * v_y, sxy = m * (u_y + v_x);
+  T* out = sig + (long long)rhs * 4 * g.field + pc;
+  out[0] = a0 * sxx + a1 * sxy;
+  out[g.field] = a2 * sxx + a3 * sxy;
+  out[2 * g.field] = a0 * sxy + a1 * syy;
+  out[3 * g.field] = a2 * sxy + a3 * syy;
+}
+
+template <typename T, int MODE, bool FORCED>
+__global__ void __launch_bounds__(256) curv_div2d(Geom g, WaveFields<T> f, StepScalars s) {
+  if (g.dim != 2) return;
+  pdl_wait();
+  pdl_trigger();
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int rhs = blockIdx.z;
+  if (!is_unknown(g, x, y, 0)) return;
+  const long long sy = g.np[0];
+  const long long pc = pidx(g, 0, 0, x, y, 0);
+  const T* fqu = f.sigma + (long long)rhs * 4 * g.field + pc;
+  const T* fru = fqu + g.field;
+  const T* fqv = fqu + 2 * g.field;
+  const T* frv = fqu + 3 * g.field;
+  T ku = -sbp_d1<T>(fqu, 1, x, g.n[0]) - sbp_d1<T>(fru, sy, y, g.n[1]);
+  T kv = -sbp_d1<T>(fqv, 1, x, g.n[0]) - sbp_d1<T>(frv, sy, y, g.n[1]);
+  const T inv_h0 = T(48.0 / 17.0);
+  if (x == 0) {
+    ku -= inv_h0 * fqu[0];
+    kv -= inv_h0 * fqv[0];
+  } else if (x == g.n[0] - 1) {
+    ku += inv_h0 * fqu[0];
+    kv += inv_h0 * fqv[0];
+  }
+  if (y == 0) {
+    ku -= inv_h0 * fru[0];
+    kv -= inv_h0 * frv[0];
+  } else if (y == g.n[1] - 1) {
+    ku += inv_h0 * fru[0];
+    kv += inv_h0 * frv[0];
+  }
+  const T irh = f.irh2[pc];  // 1 / (rho J h^2)
+  const long long p0 = pidx(g, rhs, 0, x, y, 0);
+  leapfrog_update<T, MODE, FORCED>(f, p0, f.u_cur[p0], ku * irh, s);
+  leapfrog_update<T, MODE, FORCED>(f, p0 + g.field, f.u_cur[p0 + g.field], kv * irh, s);
+}
+
+// Metric terms of a mapped grid (FP64, dense C-order planes, x fastest):
+// x_q, x_r, y_q, y_r from the SBP first derivative over the node spacing h,
+// J = x_q y_r - x_r y_q; out holds the planes (y_r, -x_r, -y_q, x_q, 1/J, J).
+__global__ void curv_metrics_kernel(int n0, int n1, double h, const double* __restrict__ X,
+                                    const double* __restrict__ Y, double* __restrict__ out) {
+  const long long total = (long long)n0 * n1;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % n0), y = (int)(i / n0);
+    const double xq = sbp_d1<double>(X + i, 1, x, n0) / h, xr = sbp_d1<double>(X + i, n0, y, n1) / h;
+    const double yq = sbp_d1<double>(Y + i, 1, x, n0) / h, yr = sbp_d1<double>(Y + i, n0, y, n1) / h;
+    const double J = xq * yr - xr * yq;
+    out[i] = yr;
+    out[total + i] = -xr;
+    out[2 * total + i] = -yq;
+    out[3 * total + i] = xq;
+    out[4 * total + i] = 1.0 / J;
+    out[5 * total + i] = J;
+  }
+}
+
+cudaError_t launch_curv_metrics(int n0, int n1, double h, const double* X, const double* Y, double* out,
+                                cudaStream_t st) {
+  const long long total = (long long)n0 * n1;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+  curv_metrics_kernel<<<blocks, 256, 0, st>>>(n0, n1, h, X, Y, out);
+  return cudaGetLastError();
+}
+
 template <typename T, int MODE, bool FORCED, int TX, int TY>
 static cudaError_t launch_split_o4(const Geom& g, const WaveFields<T>& f, const StepScalars& s, cudaStream_t st) {
   dim3 tgrd((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, g.nrhs);
@@ -701,6 +810,15 @@ static cudaError_t launch_mode(const Geom& g, int order, const WaveFields<T>& f,
       if (e != cudaSuccess) return e;
     }
     if (nl) *nl += 1;
+    return cudaGetLastError();
+  }
+  if (g.mapped) {  // curvilinear 2D order 4
+    dim3 blk(32, 8), grd((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.nrhs);
+    cudaError_t e = launch_k(curv_stress2d<T>, grd, blk, st, g, (const T*)f.u_cur, f.lam, f.mu, f.met, f.sigma);
+    if (e != cudaSuccess) return e;
+    e = launch_k(curv_div2d<T, MODE, FORCED>, grd, blk, st, g, f, s);
+    if (e != cudaSuccess) return e;
+    if (nl) *nl += 2;
     return cudaGetLastError();
   }
   if (g.dim == 2 && step2d_o4_variant(g) == 1) {
@@ -749,8 +867,9 @@ cudaError_t launch_step(const Geom& g, int order, const WaveFields<T>& f, StepMo
 
 template <typename T>
 cudaError_t launch_minvK(const Geom& g, int order, const T* u, T* out, const T* lam, const T* mu,
-                         const T* irh2, T* sigma, cudaStream_t st, long long* nl) {
+                         const T* irh2, T* sigma, cudaStream_t st, long long* nl, const T* met) {
   WaveFields<T> f{};
+  f.met = met;
   f.u_cur = const_cast<T*>(u);
   f.u_next = out;
   f.lam = lam;
@@ -1483,8 +1602,9 @@ template cudaError_t launch_step<float>(const Geom&, int, const WaveFields<float
 template cudaError_t launch_step<double>(const Geom&, int, const WaveFields<double>&, StepMode,
                                          const StepScalars&, cudaStream_t, long long*);
 template cudaError_t launch_minvK<float>(const Geom&, int, const float*, float*, const float*, const float*,
-                                         const float*, float*, cudaStream_t, long long*);
+                                         const float*, float*, cudaStream_t, long long*, const float*);
 template cudaError_t launch_minvK<double>(const Geom&, int, const double*, double*, const double*,
-                                          const double*, const double*, double*, cudaStream_t, long long*);
+                                          const double*, const double*, double*, cudaStream_t, long long*,
+                                          const double*);
 
 }  // namespace ewh

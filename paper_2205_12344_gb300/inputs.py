@@ -255,6 +255,29 @@ def small_problem(dim, nu, order, bc, seed=0, nrhs=1, omega=None, h=None):
                    float(omega), rho, lam, mu, forcing)
 
 
+def annulus_mapping(n, h, span=math.pi / 3, r0=1.0, dr=0.5):
+    """Node coordinates (x, y), each of full_shape(n), of an annular sector: the
+    radius r0 + dr q' along q and the angle span r' along r (q', r' in [0, 1]
+    over the grid), so the mapping preserves orientation."""
+    q = np.arange(n[0]) / (n[0] - 1)
+    r = np.arange(n[1]) / (n[1] - 1)
+    Q, R = np.meshgrid(q, r)
+    rad = r0 + dr * Q
+    ang = span * R
+    return rad * np.cos(ang), rad * np.sin(ang)
+
+
+def wavy_mapping(n, h, amp=0.04):
+    """Node coordinates of a smoothly skewed, non-orthogonal square: x = q +
+    amp L sin(2 pi r / L) + (amp L / 2) sin(pi q / L) sin(pi r / L),
+    y = r + amp L sin(2 pi q / L), L the side length (n - 1) h per axis."""
+    Lq, Lr = (n[0] - 1) * h, (n[1] - 1) * h
+    Q, R = np.meshgrid(np.arange(n[0]) * h, np.arange(n[1]) * h)
+    X = Q + amp * Lq * np.sin(2 * np.pi * R / Lr) + 0.5 * amp * Lq * np.sin(np.pi * Q / Lq) * np.sin(np.pi * R / Lr)
+    Y = R + amp * Lr * np.sin(2 * np.pi * Q / Lq)
+    return X, Y
+
+
 def random_vectors(prob: Problem, count: int, seed: int) -> np.ndarray:
     """``count`` random unknown-vectors (float64), shape [count][nrhs*dim*nodes]."""
     rng = np.random.default_rng(seed)
