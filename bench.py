@@ -59,6 +59,8 @@ def parse():
                     help="skip the plain FP64 GPU solve used for the time-to-tol comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 192-system measurement")
     ap.add_argument("--batch-iters", type=int, default=24, help="batched CG iterations timed")
+    ap.add_argument("--no-mapped", action="store_true", help="skip the mapped-grid (annular sector) measurement")
+    ap.add_argument("--mapped-applies", type=int, default=4, help="S applies timed per precision on the mapped grid")
     return ap.parse_args()
 
 
@@ -270,6 +272,64 @@ def batch_measurement(iters, stream):
             "max_rel_res": max(i.rel_res for i in infos)}
 
 
+ALG_BYTES_MAPPED = {"fp32": 68.0, "fp64": 136.0}   # 52 (104) B plus the 4 metric planes per node
+
+
+def mapped_workload(nu):
+    """The benchmark's layered medium and source on a curvilinear grid: the
+    (q, r) square mapped onto an annular sector of about the same extent
+    (radius 1.5 L .. 2.5 L along q, 0.5 rad along r; L the side length)."""
+    from paper_2205_12344_gb300 import inputs
+    p = workload(nu, 0, 1)
+    L = (p.n[0] - 1) * p.h
+    p.mapping = inputs.annulus_mapping(p.n, p.h, span=0.5, r0=1.5 * L, dr=L)
+    return p
+
+
+def mapped_measurement(nu, applies, stream, flush):
+    """Throughput of the mapped-grid step (curvilinear order-4 SBP, Section
+    4.1) on the layered workload mapped onto an annular sector: ``applies`` S
+    applies per precision, device time of the wave solves from the library's
+    own CUDA events, the autotuner's kernel (0 = fused, 1 = stress + divergence)."""
+    import torch
+    from paper_2205_12344_gb300 import _lib as L
+    from paper_2205_12344_gb300.api import WaveHoltz
+    prob = mapped_workload(nu)
+    out = {"workload": "layered2d_%d on an annular sector (mapped grid), order-4 SBP, S applies" % nu}
+    peak, peak_kind = peaks()
+    for prec, idx in (("fp32", 1), ("fp64", 0)):
+        with WaveHoltz(prob, precision=prec) as wh:
+            g = torch.Generator(device="cuda").manual_seed(3)
+            v = torch.randn(wh.n, dtype=torch.float64, device="cuda", generator=g)
+            wh.apply_S(v)                                    # warm: autotuner, graph
+            torch.cuda.synchronize()
+            wh.reset_stats()
+            ms = 0.0
+            for _ in range(applies):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                wh.apply_S(v)
+                e1.record(stream)
+                e1.synchronize()
+                ms += e0.elapsed_time(e1)
+            st = wh.stats()
+            nodes = int(wh.info.nodes)
+            step_ms = st.wave_ms[idx] / max(st.steps[idx], 1)
+            achieved = ALG_BYTES_MAPPED[prec] * nodes / (step_ms * 1e-3) / 1e9
+            variant = int(L.ewh_get_info(wh.ctx).kernel_variant[idx])
+            out[prec] = {"value": st.steps[idx] * nodes / (ms * 1e-3) / 1e9, "unit": UNIT, "nt": int(wh.info.nt),
+                         "nodes": nodes, "applies": applies, "step_ms": step_ms,
+                         "kernel": "curv_step2d (fused)" if variant == 0 else "curv_stress2d + curv_div2d",
+                         "kernel_variant": variant,
+                         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                      "frac": achieved / peak, "peak_source": peak_kind,
+                                      "alg_bytes_per_node_step": ALG_BYTES_MAPPED[prec]},
+                         "gpu_launches": int(st.launches)}
+    return out
+
+
 def run_reference(args, ws, rank):
     """--impl reference: the FP64 CPU oracle as it stands, on host cores."""
     if rank != 0:
@@ -390,6 +450,8 @@ def main():
         if not args.no_batch:
             flush.fill_(1.0)
             extra["batch"] = batch_measurement(args.batch_iters, stream)
+        if not args.no_mapped:
+            extra["mapped"] = mapped_measurement(args.nu, args.mapped_applies, stream, flush)
     wh.close()
 
     # end to end through the C ABI with host buffers: create (H2D of medium and

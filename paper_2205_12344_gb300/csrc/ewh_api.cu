@@ -35,7 +35,7 @@ struct Wave {
   T* irh2 = nullptr;
   T* frho = nullptr;   // null when the problem has no forcing
   T* sigma = nullptr;  // order 4 only (mapped grids: the four fluxes)
-  T* met = nullptr;    // mapped grids: metric planes (y_r, -x_r, -y_q, x_q, 1/J)
+  T* met = nullptr;    // mapped grids: metric planes (y_r, -x_r, -y_q, x_q); lam, mu hold lambda / J, mu / J
   cudaGraphExec_t graph_S = nullptr;
   cudaGraphExec_t graph_Pi0 = nullptr;
   long long graph_S_kernels = 0;
@@ -178,10 +178,10 @@ ewh_status build_wave(ewh_ctx* ctx, Wave<T>& w, const double* d_rho, const doubl
   const int blocks = (int)std::min<long long>((full + 255) / 256, 4096);
   const double h2 = ctx->h * ctx->h;
   if (g.mapped) {
-    EWH_CU(alloc_zero(&w.met, field * 5, ctx->st));
-    for (int k = 0; k < 5; ++k)
+    EWH_CU(alloc_zero(&w.met, field * 4, ctx->st));
+    for (int k = 0; k < 4; ++k)
       to_padded_kernel<T><<<blocks, 256, 0, ctx->st>>>(g, d_met + (size_t)k * full, d_rho, 0, h2, w.met + k * field);
-    ctx->launches += 5;
+    ctx->launches += 4;
   }
   to_padded_kernel<T><<<blocks, 256, 0, ctx->st>>>(g, d_lam, d_rho, 0, h2, w.lam);
   to_padded_kernel<T><<<blocks, 256, 0, ctx->st>>>(g, d_mu, d_rho, 0, h2, w.mu);
@@ -312,7 +312,8 @@ std::string tune_key(const ewh_ctx* ctx) {
   for (auto& ch : name)
     if (ch == '"' || ch == ' ') ch = '_';
   const Geom& g = ctx->g;
-  return name + "|v3" + (ctx->allow_resident ? "" : "b") + "|d" + std::to_string(g.dim) + "|o" + std::to_string(ctx->order) + "|" +
+  return name + "|v3" + (ctx->allow_resident ? "" : "b") + (g.mapped ? "|map" : "") + "|d" + std::to_string(g.dim) +
+         "|o" + std::to_string(ctx->order) + "|" +
          (sizeof(T) == 8 ? "f64" : "f32") + "|" + std::to_string(g.n[0]) + "x" + std::to_string(g.n[1]) + "x" +
          std::to_string(g.n[2]) + "|r" + std::to_string(g.nrhs);
 }
@@ -360,7 +361,7 @@ cudaError_t enqueue_resident(ewh_ctx* ctx, Wave<T>& w, int v, bool forced, int n
 
 template <typename T>
 void autotune(ewh_ctx* ctx, Wave<T>& w) {
-  const int nbase = step_variant_count(ctx->g.dim, ctx->order);
+  const int nbase = ctx->g.mapped ? 3 : step_variant_count(ctx->g.dim, ctx->order);
   const char* force = getenv("EWH_STEP2D_O4");
   const bool forced_launcher = force && (force[0] == 's' || force[0] == 'f');
   bool any_res = false;
@@ -375,7 +376,7 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
     }
   }
   const char* off = getenv("EWH_AUTOTUNE");
-  if (nv <= 1 || ctx->g.mapped || (off && off[0] == '0')) {  // mapped grids: one launcher
+  if (nv <= 1 || (off && off[0] == '0')) {
     w.variant = 0;
     return;
   }
@@ -1582,7 +1583,11 @@ ewh_status create_impl(const ewh_grid_desc* desc, const double* xmap, const doub
   }
   std::vector<double> hf;  // mapped grids: J f, so that (J f) / (rho J) = f / rho
   if (mapped) {
-    for (long long i = 0; i < full; ++i) hr[i] *= hmet[5 * full + i];  // the mass density rho J
+    for (long long i = 0; i < full; ++i) {
+      hr[i] *= hmet[5 * full + i];  // the mass density rho J
+      hl[i] *= hmet[4 * full + i];  // lambda / J and mu / J: the stress kernels take
+      hm[i] *= hmet[4 * full + i];  // J times the physical gradient
+    }
     if (forcing) {
       hf.resize((size_t)full * dim * nrhs);
       cudaPointerAttributes at;

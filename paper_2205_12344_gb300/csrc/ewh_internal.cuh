@@ -79,7 +79,7 @@ struct WaveFields {
   const T* irh2;   // 1 / (rho h^2)
   const T* frho;   // f / rho per rhs and component, or nullptr (S apply)
   T* sigma;        // order-4 stress scratch (dim*(dim+1)/2 fields per rhs) or nullptr
-  const T* met = nullptr;  // mapped grids: 5 planes (y_r, -x_r, -y_q, x_q, 1/J) of one padded component
+  const T* met = nullptr;  // mapped grids: 4 planes (y_r, -x_r, -y_q, x_q) of one padded component
 };
 
 // ---- launchers (ewh_stencil.cu) -------------------------------------------

@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 
 #include "ewh_internal.cuh"
 
@@ -103,6 +104,34 @@ __device__ __forceinline__ void leapfrog_update(const WaveFields<T>& f, long lon
     f.acc[p] += T(s.wnew) * un;
   }
 }
+
+// The same update with delta^n, acc and f/rho already loaded (dprev, accprev
+// are not read at the first level; fr only when FORCED).
+template <typename T, int MODE, bool FORCED>
+__device__ __forceinline__ void leapfrog_update_pre(const WaveFields<T>& f, long long p, T uval, T a,
+                                                    const StepScalars& s, T dprev, T accprev, T fr) {
+  if (MODE == 3) {
+    f.u_next[p] = a;
+    return;
+  }
+  if (FORCED) a += fr * T(s.cosn);
+  if (MODE == STEP_FIRST) {
+    const T d = T(-0.5) * T(s.kt) * a;
+    const T un = uval + d;
+    f.delta[p] = d;
+    f.u_next[p] = un;
+    f.acc[p] = T(s.w0) * uval + T(s.wnew) * un;
+  } else {
+    const T d = dprev - T(s.kt) * a;
+    const T un = uval + d;
+    if (MODE == STEP_MID) {
+      f.delta[p] = d;
+      f.u_next[p] = un;
+    }
+    f.acc[p] = accprev + T(s.wnew) * un;
+  }
+}
+
 
 // ---------------------------------------------------------------------------
 // Order 2, 2D: 32 x 8 tile, one node per thread, halo 1 in shared memory.
@@ -662,6 +691,16 @@ static cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cud
 // 64x4 blocks, 4 = single fused launch.  EWH_STEP2D_O4=fused|split overrides
 // it (read whenever launches are enqueued; a context captures its step graph
 // once, on first use).
+// Mapped 2D grids: 0 = fused curv_step2d with 32x8 outputs per block, 1 =
+// curv_stress2d + curv_div2d, 2 = fused with 32x16 outputs (FP32; FP64 runs 32x8).  Geom::variant
+// from the autotuner; EWH_CURV=fused|fused16|split overrides it.
+static int curv_variant(const Geom& g) {
+  const char* e = getenv("EWH_CURV");
+  if (e && e[0] == 'f') return strcmp(e, "fused16") == 0 ? 2 : 0;
+  if (e && e[0] == 's') return 1;
+  return (g.variant == 1 || g.variant == 2) ? g.variant : 0;
+}
+
 static int step2d_o4_variant(const Geom& g) {
   const char* e = getenv("EWH_STEP2D_O4");
   if (e && e[0] == 'f') return 1;
@@ -679,13 +718,14 @@ static int step2d_o4_tile(const Geom& g) {
 // node grid is the image of (q, r) = (i h, j h) under a smooth mapping.  The
 // stress kernel forms physical derivatives from the SBP derivatives in q and
 // r, u_x = (y_r u_q - y_q u_r) / J, u_y = (x_q u_r - x_r u_q) / J, the
-// stresses, and the four J-weighted fluxes
+// stresses (the 1/J rides on lambda / J and mu / J, which the context stores
+// in place of lambda and mu), and the four J-weighted fluxes
 //   F^q_u = y_r s_xx - x_r s_xy,  F^r_u = -y_q s_xx + x_q s_xy,
 //   F^q_v = y_r s_xy - x_r s_yy,  F^r_v = -y_q s_xy + x_q s_yy;
 // the divergence kernel forms -D_q F^q - D_r F^r + H^{-1} B F (the Cartesian
 // kernel with the fluxes in place of the stresses) times 1/(rho J h^2).
 // One node per thread, global memory (the grid sizes of mapped problems are
-// moderate); the metric planes are (y_r, -x_r, -y_q, x_q, 1/J).
+// moderate); the metric planes are (y_r, -x_r, -y_q, x_q).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) curv_stress2d(Geom g, const T* __restrict__ u, const T* __restrict__ lam,
@@ -704,10 +744,9 @@ __global__ void __launch_bounds__(256) curv_stress2d(Geom g, const T* __restrict
   const T uq = sbp_d1<T>(U, 1, x, g.n[0]), ur = sbp_d1<T>(U, sy, y, g.n[1]);
   const T vq = sbp_d1<T>(V, 1, x, g.n[0]), vr = sbp_d1<T>(V, sy, y, g.n[1]);
   const T a0 = met[pc], a1 = met[g.field + pc], a2 = met[2 * g.field + pc], a3 = met[3 * g.field + pc];
-  const T ij = met[4 * g.field + pc];
-  const T u_x = (a0 * uq + a2 * ur) * ij, u_y = (a1 * uq + a3 * ur) * ij;
-  const T v_x = (a0 * vq + a2 * vr) * ij, v_y = (a1 * vq + a3 * vr) * ij;
-  const T l = lam[pc], m = mu[pc];
+  const T u_x = a0 * uq + a2 * ur, u_y = a1 * uq + a3 * ur;  // J times the physical gradient
+  const T v_x = a0 * vq + a2 * vr, v_y = a1 * vq + a3 * vr;
+  const T l = lam[pc], m = mu[pc];                            // lambda / J, mu / J
   const T div = u_x + v_y;
   const T sxx = l * div + T(2) * m * u_x, syy = l * div + T(2) * m * v_y, sxy = m * (u_y + v_x);
   T* out = sig + (long long)rhs * 4 * g.field + pc;
@@ -752,6 +791,185 @@ __global__ void __launch_bounds__(256) curv_div2d(Geom g, WaveFields<T> f, StepS
   const long long p0 = pidx(g, rhs, 0, x, y, 0);
   leapfrog_update<T, MODE, FORCED>(f, p0, f.u_cur[p0], ku * irh, s);
   leapfrog_update<T, MODE, FORCED>(f, p0 + g.field, f.u_cur[p0 + g.field], kv * irh, s);
+}
+
+// Fused form of the two kernels above: one launch per time level, blocks of
+// 32 x 8 threads and 32 x (8 RPT) output nodes (RPT rows per thread).  The
+// block stages u (both components) and the six coefficient planes (y_r, -x_r,
+// -y_q, x_q, lambda / J, mu / J) on a tile of (32 + 6) x (8 RPT + 6) nodes in
+// shared memory, then forms the four fluxes in place of the first four
+// planes.  The tile starts 2 nodes before the block, or at n - 6 when that is
+// lower, so it holds every flux a central or SBP-closure difference of the
+// block's nodes reads.  Blocks whose tile lies in rows and columns 4 .. n - 5
+// (every difference central, every node an unknown) take a path with no
+// per-node tests; the others difference fluxes at nodes within 4 of a side
+// with the SBP closure applied to u in global memory.  Every load is issued
+// before the first barrier: the coefficients (static) ahead of the wait on the
+// previous level, the state and the update's operands after it.
+template <typename T, int MODE, bool FORCED, int RPT>
+__global__ void __launch_bounds__(256) curv_step2d(Geom g, WaveFields<T> f, StepScalars s) {
+  if (g.dim != 2) return;
+  constexpr int TX = 32, TY = 8 * RPT;
+  constexpr int FX = TX + 6, FY = TY + 6;  // flux / coefficient tile
+  constexpr int UX = FX + 4, UY = FY + 4;  // u tile: 2-node reach of the central fluxes
+  __shared__ T su[2][UY][UX];
+  __shared__ T sc[6][FY][FX];
+  const int nx = g.n[0], ny = g.n[1];
+  const int rhs = blockIdx.z;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int xs = min(x0 - 2, nx - 6), ys = min(y0 - 2, ny - 6);
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int sy = g.np[0];
+  const int fld = (int)g.field;  // one padded component indexes in 32 bits
+  const bool inner = xs >= 4 && xs + FX - 1 <= nx - 5 && ys >= 4 && ys + FY - 1 <= ny - 5;
+  const long long cbase = pidx(g, 0, 0, xs, ys, 0);  // coefficient tile origin
+  const T* M0 = f.met + cbase;
+  const T* LA = f.lam + cbase;
+  const T* MU = f.mu + cbase;
+  if (inner) {
+    for (int r = ty; r < FY; r += 8)
+      for (int c = tx; c < FX; c += 32) {
+        const int q = r * sy + c;
+        sc[0][r][c] = M0[q];
+        sc[1][r][c] = M0[fld + q];
+        sc[2][r][c] = M0[2 * fld + q];
+        sc[3][r][c] = M0[3 * fld + q];
+        sc[4][r][c] = LA[q];
+        sc[5][r][c] = MU[q];
+      }
+  } else {
+    for (int r = ty; r < FY; r += 8)
+      for (int c = tx; c < FX; c += 32) {
+        const int gx = xs + c, gy = ys + r;
+        const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+        const int q = r * sy + c;
+        sc[0][r][c] = in ? M0[q] : T(0);
+        sc[1][r][c] = in ? M0[fld + q] : T(0);
+        sc[2][r][c] = in ? M0[2 * fld + q] : T(0);
+        sc[3][r][c] = in ? M0[3 * fld + q] : T(0);
+        sc[4][r][c] = in ? LA[q] : T(0);
+        sc[5][r][c] = in ? MU[q] : T(0);
+      }
+  }
+  // this thread's output nodes: (x0 + tx, y0 + ty + 8 k)
+  const int x = x0 + tx;
+  const long long p00 = pidx(g, rhs, 0, x, y0 + ty, 0);
+  const long long c00 = pidx(g, 0, 0, x, y0 + ty, 0);
+  bool unk[RPT];
+  T irh[RPT], fr0[RPT], fr1[RPT];
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    unk[k] = inner || is_unknown(g, x, y0 + ty + 8 * k, 0);
+    irh[k] = unk[k] ? f.irh2[c00 + 8 * k * sy] : T(0);  // 1 / (rho J h^2)
+    fr0[k] = (FORCED && unk[k]) ? f.frho[p00 + 8 * k * sy] : T(0);
+    fr1[k] = (FORCED && unk[k]) ? f.frho[p00 + 8 * k * sy + fld] : T(0);
+  }
+  pdl_wait();
+  pdl_trigger();
+  const T* U0 = f.u_cur + pidx(g, rhs, 0, 0, 0, 0);
+  {
+    const T* Ut = f.u_cur + pidx(g, rhs, 0, xs - 2, ys - 2, 0);  // inside the padding (PAD >= 4)
+    for (int r = ty; r < UY; r += 8)
+      for (int c = tx; c < UX; c += 32) {
+        const int gx = xs - 2 + c, gy = ys - 2 + r;
+        const bool in = inner || (gx >= 0 && gx < nx && gy >= 0 && gy < ny);
+        const int q = r * sy + c;
+        su[0][r][c] = in ? Ut[q] : T(0);
+        su[1][r][c] = in ? Ut[fld + q] : T(0);
+      }
+  }
+  T d0[RPT], d1[RPT], ac0[RPT], ac1[RPT];
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const bool ld = MODE != 3 && MODE != STEP_FIRST && unk[k];
+    const long long p = p00 + 8 * k * sy;
+    d0[k] = ld ? f.delta[p] : T(0);
+    d1[k] = ld ? f.delta[p + fld] : T(0);
+    ac0[k] = ld ? f.acc[p] : T(0);
+    ac1[k] = ld ? f.acc[p + fld] : T(0);
+  }
+  __syncthreads();
+  for (int r = ty; r < FY; r += 8)
+    for (int c = tx; c < FX; c += 32) {
+      const int gx = xs + c, gy = ys + r;
+      T uq, ur, vq, vr;
+      const int ux = c + 2, uy = r + 2;
+      if (inner || (gx >= 4 && gx <= nx - 5)) {
+        uq = c4(su[0][uy][ux - 2], su[0][uy][ux - 1], su[0][uy][ux + 1], su[0][uy][ux + 2]);
+        vq = c4(su[1][uy][ux - 2], su[1][uy][ux - 1], su[1][uy][ux + 1], su[1][uy][ux + 2]);
+      } else {
+        if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) continue;  // never read
+        const long long q = (long long)gy * sy + gx;
+        uq = sbp_d1<T>(U0 + q, 1, gx, nx);
+        vq = sbp_d1<T>(U0 + fld + q, 1, gx, nx);
+      }
+      if (inner || (gy >= 4 && gy <= ny - 5)) {
+        ur = c4(su[0][uy - 2][ux], su[0][uy - 1][ux], su[0][uy + 1][ux], su[0][uy + 2][ux]);
+        vr = c4(su[1][uy - 2][ux], su[1][uy - 1][ux], su[1][uy + 1][ux], su[1][uy + 2][ux]);
+      } else {
+        if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) continue;  // never read
+        const long long q = (long long)gy * sy + gx;
+        ur = sbp_d1<T>(U0 + q, sy, gy, ny);
+        vr = sbp_d1<T>(U0 + fld + q, sy, gy, ny);
+      }
+      const T a0 = sc[0][r][c], a1 = sc[1][r][c], a2 = sc[2][r][c], a3 = sc[3][r][c];
+      const T l = sc[4][r][c], m = sc[5][r][c];
+      const T u_x = a0 * uq + a2 * ur, u_y = a1 * uq + a3 * ur;
+      const T v_x = a0 * vq + a2 * vr, v_y = a1 * vq + a3 * vr;
+      const T div = u_x + v_y;
+      const T sxx = l * div + T(2) * m * u_x, syy = l * div + T(2) * m * v_y, sxy = m * (u_y + v_x);
+      sc[0][r][c] = a0 * sxx + a1 * sxy;
+      sc[1][r][c] = a2 * sxx + a3 * sxy;
+      sc[2][r][c] = a0 * sxy + a1 * syy;
+      sc[3][r][c] = a2 * sxy + a3 * syy;
+    }
+  __syncthreads();
+  const int lx = x - xs;
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    if (!unk[k]) continue;
+    const int y = y0 + ty + 8 * k;
+    const int ly = y - ys;
+    const T* fqu = &sc[0][ly][lx];
+    const T* fru = &sc[1][ly][lx];
+    const T* fqv = &sc[2][ly][lx];
+    const T* frv = &sc[3][ly][lx];
+    T ku, kv;
+    if (inner || (x >= 4 && x <= nx - 5)) {
+      ku = -c4(fqu[-2], fqu[-1], fqu[1], fqu[2]);
+      kv = -c4(fqv[-2], fqv[-1], fqv[1], fqv[2]);
+    } else {
+      ku = -sbp_d1<T>(fqu, 1, x, nx);
+      kv = -sbp_d1<T>(fqv, 1, x, nx);
+    }
+    if (inner || (y >= 4 && y <= ny - 5)) {
+      ku -= c4(fru[-2 * FX], fru[-FX], fru[FX], fru[2 * FX]);
+      kv -= c4(frv[-2 * FX], frv[-FX], frv[FX], frv[2 * FX]);
+    } else {
+      ku -= sbp_d1<T>(fru, FX, y, ny);
+      kv -= sbp_d1<T>(frv, FX, y, ny);
+    }
+    if (!inner) {
+      const T inv_h0 = T(48.0 / 17.0);
+      if (x == 0) {
+        ku -= inv_h0 * fqu[0];
+        kv -= inv_h0 * fqv[0];
+      } else if (x == nx - 1) {
+        ku += inv_h0 * fqu[0];
+        kv += inv_h0 * fqv[0];
+      }
+      if (y == 0) {
+        ku -= inv_h0 * fru[0];
+        kv -= inv_h0 * frv[0];
+      } else if (y == ny - 1) {
+        ku += inv_h0 * fru[0];
+        kv += inv_h0 * frv[0];
+      }
+    }
+    const long long p = p00 + 8 * k * sy;
+    leapfrog_update_pre<T, MODE, FORCED>(f, p, su[0][ly + 2][lx + 2], ku * irh[k], s, d0[k], ac0[k], fr0[k]);
+    leapfrog_update_pre<T, MODE, FORCED>(f, p + fld, su[1][ly + 2][lx + 2], kv * irh[k], s, d1[k], ac1[k], fr1[k]);
+  }
 }
 
 // Metric terms of a mapped grid (FP64, dense C-order planes, x fastest):
@@ -812,7 +1030,21 @@ static cudaError_t launch_mode(const Geom& g, int order, const WaveFields<T>& f,
     if (nl) *nl += 1;
     return cudaGetLastError();
   }
-  if (g.mapped) {  // curvilinear 2D order 4
+  if (g.mapped) {  // curvilinear 2D order 4: fused 32x8 (0) or 32x16 (2, FP32), stress + divergence (1)
+    const int cv = curv_variant(g);
+    if (cv != 1) {
+      cudaError_t e;
+      if (cv == 2 && sizeof(T) == 4) {  // 32 x 16 outputs per block
+        dim3 blk(32, 8), grd((g.n[0] + 31) / 32, (g.n[1] + 15) / 16, g.nrhs);
+        e = launch_k(curv_step2d<T, MODE, FORCED, sizeof(T) == 4 ? 2 : 1>, grd, blk, st, g, f, s);
+      } else {
+        dim3 blk(32, 8), grd((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.nrhs);
+        e = launch_k(curv_step2d<T, MODE, FORCED, 1>, grd, blk, st, g, f, s);
+      }
+      if (e != cudaSuccess) return e;
+      if (nl) *nl += 1;
+      return cudaGetLastError();
+    }
     dim3 blk(32, 8), grd((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.nrhs);
     cudaError_t e = launch_k(curv_stress2d<T>, grd, blk, st, g, (const T*)f.u_cur, f.lam, f.mu, f.met, f.sigma);
     if (e != cudaSuccess) return e;

@@ -8,6 +8,10 @@ library's own kernels; the state is ~60 MB per right-hand side in FP32, so a
 capture of one or two launches stays small.
 
     python -m paper_2205_12344_gb300.profile_case --nu 1024 --nrhs 1 --precision fp32 --applies 2
+
+With ``--mapping annulus`` the same medium sits on a curvilinear grid: the
+(q, r) square mapped onto an annular sector of about the same extent (the
+mapped-grid step kernels of Section 4.1).
 """
 from __future__ import annotations
 
@@ -20,6 +24,7 @@ def main(argv=None):
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides (shots) per launch")
     ap.add_argument("--precision", default="fp32", choices=("fp32", "fp64"))
     ap.add_argument("--applies", type=int, default=2, help="applications of S")
+    ap.add_argument("--mapping", default="none", choices=("none", "annulus"), help="curvilinear grid")
     a = ap.parse_args(argv)
 
     import torch
@@ -28,6 +33,9 @@ def main(argv=None):
     from .api import WaveHoltz
 
     p = inputs.cfg_layered_2d(nu=a.nu, order=4, nrhs=a.nrhs, shot_x=[2.0 + 1.5 * k for k in range(a.nrhs)])
+    if a.mapping == "annulus":
+        L = (p.n[0] - 1) * p.h
+        p.mapping = inputs.annulus_mapping(p.n, p.h, span=0.5, r0=1.5 * L, dr=L)
     with WaveHoltz(p, precision=a.precision) as wh:
         g = torch.Generator(device="cuda").manual_seed(7)
         v = torch.randn(wh.n, dtype=torch.float64, device="cuda", generator=g)

@@ -31,7 +31,9 @@ MAPS = {"annulus": inputs.annulus_mapping, "wavy": inputs.wavy_mapping,
 # (mapping, interior nodes, bc, nrhs): ragged 32 x 8 tiles, every side type
 CASES = [("annulus", [10, 9], [D, D, D, D], 1), ("annulus", [41, 13], [D, D, D, F], 2),
          ("wavy", [12, 35], [F, F, D, F], 1), ("wavy", [6, 6], [F, F, F, F], 1),
-         ("identity", [9, 10], [F, D, D, F], 1)]
+         ("identity", [9, 10], [F, D, D, F], 1), ("annulus", [130, 67], [F, D, D, D], 1)]
+# the fused one-launch step and the stress + divergence pair
+KERNELS = ["fused", "fused16", "split"]
 
 
 def _ids(c):
@@ -50,8 +52,10 @@ def _wh(p, precision="fp64", nt=0):
     return WaveHoltz(p, precision=precision, nt=nt)
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("case", CASES, ids=[_ids(c) for c in CASES])
-def test_mapped_setup_and_operator_match_oracle(case):
+def test_mapped_setup_and_operator_match_oracle(case, kernel, monkeypatch):
+    monkeypatch.setenv("EWH_CURV", kernel)
     mapname, nu, bc, nrhs = case
     p = _problem(mapname, nu, bc, nrhs)
     s = O.build_system(p)
@@ -64,8 +68,10 @@ def test_mapped_setup_and_operator_match_oracle(case):
     assert rel_err(got, want) < 1e-12
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("case", CASES, ids=[_ids(c) for c in CASES])
-def test_mapped_S_and_Pi0_match_oracle(case):
+def test_mapped_S_and_Pi0_match_oracle(case, kernel, monkeypatch):
+    monkeypatch.setenv("EWH_CURV", kernel)
     mapname, nu, bc, nrhs = case
     p = _problem(mapname, nu, bc, nrhs)
     s = O.build_system(p)
@@ -82,6 +88,20 @@ def test_mapped_S_and_Pi0_match_oracle(case):
         got64 = to_np(wh.apply_S(v, fp64=True))
     assert rel_err(got32, want) < tol32(s.nt), rel_err(got32, want)
     assert rel_err(got64, want) < TOL64
+
+
+def test_mapped_autotuner_picks_a_mapped_kernel(monkeypatch):
+    """The autotuner times the two mapped kernels (never a Cartesian variant
+    cached for the same grid size) and the pick matches the oracle."""
+    from paper_2205_12344_gb300 import _lib as L
+    monkeypatch.delenv("EWH_CURV", raising=False)
+    p = _problem("wavy", [70, 40], [D, D, D, F])
+    s = O.build_system(p)
+    with _wh(p, "fp32") as wh:
+        got0 = to_np(wh.apply_Pi0())
+        variant = L.ewh_get_info(wh.ctx).kernel_variant[1]
+    assert variant in (0, 1)
+    assert rel_err(got0, O.apply_Pi0(s)) < tol32(s.nt)
 
 
 def test_mapped_identity_is_the_cartesian_path():
