@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--batch-iters", type=int, default=24, help="batched CG iterations timed")
     ap.add_argument("--no-mapped", action="store_true", help="skip the mapped-grid (annular sector) measurement")
     ap.add_argument("--mapped-applies", type=int, default=4, help="S applies timed per precision on the mapped grid")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3D order-4 measurement")
+    ap.add_argument("--nu3d", type=int, default=256, help="unknowns per axis of the 3D workload")
     return ap.parse_args()
 
 
@@ -286,18 +288,20 @@ def mapped_workload(nu):
     return p
 
 
-def mapped_measurement(nu, applies, stream, flush):
-    """Throughput of the mapped-grid step (curvilinear order-4 SBP, Section
-    4.1) on the layered workload mapped onto an annular sector: ``applies`` S
-    applies per precision, device time of the wave solves from the library's
-    own CUDA events, the autotuner's kernel (0 = fused, 1 = stress + divergence)."""
+def wave_measurement(prob, label, applies, alg_bytes, stream, flush, kernels):
+    """S-apply throughput of one workload per precision: ``applies`` S applies
+    (the first FP64 one only when ``applies[prec]`` is 1), the device time of
+    the wave solves from the library's own CUDA events, the autotuner's kernel
+    variant (named by ``kernels``) and a roofline against ``alg_bytes[prec]``
+    per node-level."""
     import torch
     from paper_2205_12344_gb300 import _lib as L
     from paper_2205_12344_gb300.api import WaveHoltz
-    prob = mapped_workload(nu)
-    out = {"workload": "layered2d_%d on an annular sector (mapped grid), order-4 SBP, S applies" % nu}
+    out = {"workload": label}
     peak, peak_kind = peaks()
     for prec, idx in (("fp32", 1), ("fp64", 0)):
+        if not applies.get(prec):
+            continue
         with WaveHoltz(prob, precision=prec) as wh:
             g = torch.Generator(device="cuda").manual_seed(3)
             v = torch.randn(wh.n, dtype=torch.float64, device="cuda", generator=g)
@@ -305,7 +309,7 @@ def mapped_measurement(nu, applies, stream, flush):
             torch.cuda.synchronize()
             wh.reset_stats()
             ms = 0.0
-            for _ in range(applies):
+            for _ in range(applies[prec]):
                 flush.fill_(1.0)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
@@ -317,17 +321,39 @@ def mapped_measurement(nu, applies, stream, flush):
             st = wh.stats()
             nodes = int(wh.info.nodes)
             step_ms = st.wave_ms[idx] / max(st.steps[idx], 1)
-            achieved = ALG_BYTES_MAPPED[prec] * nodes / (step_ms * 1e-3) / 1e9
+            achieved = alg_bytes[prec] * nodes / (step_ms * 1e-3) / 1e9
             variant = int(L.ewh_get_info(wh.ctx).kernel_variant[idx])
             out[prec] = {"value": st.steps[idx] * nodes / (ms * 1e-3) / 1e9, "unit": UNIT, "nt": int(wh.info.nt),
-                         "nodes": nodes, "applies": applies, "step_ms": step_ms,
-                         "kernel": "curv_step2d (fused)" if variant == 0 else "curv_stress2d + curv_div2d",
-                         "kernel_variant": variant,
+                         "nodes": nodes, "applies": applies[prec], "step_ms": step_ms,
+                         "kernel": kernels.get(variant, "variant %d" % variant), "kernel_variant": variant,
                          "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                       "frac": achieved / peak, "peak_source": peak_kind,
-                                      "alg_bytes_per_node_step": ALG_BYTES_MAPPED[prec]},
+                                      "alg_bytes_per_node_step": alg_bytes[prec]},
                          "gpu_launches": int(st.launches)}
     return out
+
+
+def mapped_measurement(nu, applies, stream, flush):
+    """Mapped-grid step (curvilinear order-4 SBP, Section 4.1) on the layered
+    workload mapped onto an annular sector."""
+    return wave_measurement(mapped_workload(nu),
+                            "layered2d_%d on an annular sector (mapped grid), order-4 SBP, S applies" % nu,
+                            {"fp32": applies, "fp64": applies}, ALG_BYTES_MAPPED, stream, flush,
+                            {0: "curv_step2d (fused, 32x8)", 1: "curv_stress2d + curv_div2d",
+                             2: "curv_step2d (fused, 32x16)"})
+
+
+ALG_BYTES_3D = {"fp32": 72.0, "fp64": 144.0}      # read u, u_prev, acc + write u', acc (3 comps) + lambda, mu, 1/M
+
+
+def threed_measurement(nu, stream, flush):
+    """3D order-4 SBP step on the 256^3 Gaussian-random-field workload (log Vs
+    GRF, Vp = 1.8 Vs, Dirichlet, point source at the centre)."""
+    from paper_2205_12344_gb300 import inputs
+    prob = inputs.cfg_grf_3d(nu=nu, order=4)
+    return wave_measurement(prob, "grf3d_%d: 3D GRF medium %d^3 unknowns, order-4 SBP, S applies" % (nu, nu),
+                            {"fp32": 2, "fp64": 1}, ALG_BYTES_3D, stream, flush,
+                            {0: "sbp_stress + sbp_divergence_step (3D)"})
 
 
 def run_reference(args, ws, rank):
@@ -452,6 +478,8 @@ def main():
             extra["batch"] = batch_measurement(args.batch_iters, stream)
         if not args.no_mapped:
             extra["mapped"] = mapped_measurement(args.nu, args.mapped_applies, stream, flush)
+        if not args.no_3d:
+            extra["grf3d"] = threed_measurement(args.nu3d, stream, flush)
     wh.close()
 
     # end to end through the C ABI with host buffers: create (H2D of medium and
