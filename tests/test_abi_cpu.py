@@ -94,3 +94,52 @@ def test_invalid_omega_rejected(lib):
 def test_status_strings(lib):
     assert lib.ewh_status_string(0) == b"EWH_OK"
     assert lib.ewh_status_string(5) == b"EWH_EBREAKDOWN"
+
+
+def _call_create_mapped(lib, desc, X, Y, m):
+    from paper_2205_12344_gb300 import _lib
+    out = ctypes.c_void_p()
+    s = lib.ewh_create_mapped(ctypes.byref(desc), _lib._ptr(X), _lib._ptr(Y), _lib._ptr(m), _lib._ptr(m),
+                              _lib._ptr(m), 3.0, None, 1, None, ctypes.byref(out))
+    return s, out
+
+
+@pytest.mark.parametrize("case,msg", [("no_x", "x and y"), ("order2", "dim 2 and order 4"),
+                                      ("dim3", "dim 2 and order 4"), ("nan", "finite"), ("bad_desc", "h must")])
+def test_mapped_create_validates_on_the_host(lib, case, msg):
+    """ewh_create_mapped rejects missing or non-finite coordinates and grids
+    other than 2D order 4 before touching the device."""
+    from paper_2205_12344_gb300 import _lib
+    n = [10, 12, 1]
+    m = np.ones((12, 10))
+    Q, R = np.meshgrid(np.arange(10) * 0.1, np.arange(12) * 0.1)
+    kw = {"order": 4, "n": n}
+    if case == "order2":
+        kw["order"] = 2
+    if case == "dim3":
+        kw.update(dim=3, n=[10, 12, 9])
+        m = np.ones((9, 12, 10))
+        Q, R = np.ones((9, 12, 10)), np.ones((9, 12, 10))
+    if case == "bad_desc":
+        kw["h"] = -1.0
+    if case == "nan":
+        Q = Q.copy()
+        Q[3, 4] = np.nan
+    s, out = _call_create_mapped(lib, _desc(**kw), None if case == "no_x" else Q, R, m)
+    assert s == _lib.EWH_EINVAL
+    assert not out.value
+    assert msg in lib.ewh_last_error(None).decode()
+
+
+def test_mapped_create_without_device_reports_ecuda(lib):
+    """Valid arguments on a machine without a CUDA device: the metric terms
+    are computed on the device, so creation fails with EWH_ECUDA."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2205_12344_gb300 import _lib
+    m = np.ones((12, 10))
+    Q, R = np.meshgrid(np.arange(10) * 0.1, np.arange(12) * 0.1)
+    s, out = _call_create_mapped(lib, _desc(order=4, n=[10, 12, 1]), Q, R, m)
+    assert s == _lib.EWH_ECUDA
+    assert not out.value

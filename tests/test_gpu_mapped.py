@@ -8,7 +8,7 @@ import pytest
 
 from oracle import ewh_oracle as O
 from paper_2205_12344_gb300 import inputs
-from _helpers import TOL64, oracle_all_rhs, rel_err, to_np, tol32
+from _helpers import TOL64, oracle_all_rhs, rel_err, to_np, tol32, window_sample
 
 pytestmark = pytest.mark.gpu
 
@@ -163,3 +163,39 @@ def test_mapped_rejections():
     from paper_2205_12344_gb300.api import WaveHoltzBatch
     with pytest.raises(ValueError):
         WaveHoltzBatch([_problem("wavy", [8, 8], [D, D, D, D])])
+
+
+# ---------------------------------------------------------------- full size
+
+def _sector_1024():
+    """The layered 1024^2 workload mapped onto an annular sector of about the
+    same extent (radius 1.5 L .. 2.5 L along q, 0.5 rad along r)."""
+    p = inputs.cfg_layered_2d(nu=1024, order=4)
+    L = (p.n[0] - 1) * p.h
+    p.mapping = inputs.annulus_mapping(p.n, p.h, span=0.5, r0=1.5 * L, dr=L)
+    return p
+
+
+@pytest.mark.parametrize("prec,node", [("fp32", "top_left"), ("fp64", "bottom_right")])
+def test_mapped_sector_1024_sampled_parity(prec, node, monkeypatch):
+    """The mapped bench workload at full size, in the kernel the autotuner
+    picks: S v at a node near a corner from the oracle on its domain of
+    dependence (the window keeps the node coordinates, so its metric terms
+    equal the full grid's away from the window's own sides)."""
+    import math
+    monkeypatch.delenv("EWH_CURV", raising=False)
+    p = _sector_1024()
+    from paper_2205_12344_gb300.api import WaveHoltz
+    with WaveHoltz(p, precision=prec) as wh:
+        nt = wh.info.nt
+        v = inputs.random_vectors(p, 1, 31)[0]
+        got = to_np(wh.apply_S(v))
+    dtc = O.cfl_dt_mapped(p.n, p.h, p.cfl, p.rho, p.lam, p.mu, *p.mapping)
+    assert nt == max(5, int(math.ceil(2 * math.pi / p.omega / dtc)))
+    xy = (6, p.n[1] - 2) if node == "top_left" else (p.n[0] - 3, 4)
+    want = window_sample(p, nt, v, xy, reach=4)
+    idx = inputs.unknown_index(p)
+    nn = p.n_nodes()
+    gv = np.array([got[c * nn + idx[xy[1], xy[0]]] for c in range(2)])
+    tol = tol32(nt) if prec == "fp32" else TOL64
+    assert np.abs(gv - want).max() <= tol * np.abs(got).max(), (gv, want)
