@@ -430,6 +430,14 @@ __device__ __forceinline__ T c4(T m2, T m1, T p1, T p2) {
   return (m2 - T(8) * m1 + T(8) * p1 - p2) * T(1.0 / 12.0);
 }
 
+// 12 times the interior difference: the order-4 kernels that carry the
+// operator as 12 D (stresses 12 sigma, divergence 144 D sigma) apply the
+// 1 / 144 once per node, with 1 / (rho h^2), instead of once per difference.
+template <typename T>
+__device__ __forceinline__ T c4u(T m2, T m1, T p1, T p2) {
+  return m2 - T(8) * m1 + T(8) * p1 - p2;
+}
+
 // every node of the block and its 2-node reach lies in rows/columns 4..N-5
 template <int TL_TX, int TL_TY>
 __device__ __forceinline__ bool tl_block_interior(const Geom& g, int x0, int y0) {
@@ -449,10 +457,10 @@ __device__ __forceinline__ void stress2d_node(const Geom& g, const T* u, const T
   const long long pc = pidx(g, 0, 0, x, y, 0);
   const T l = lam[pc], m = mu[pc];
   const T div = u_x + v_y;
-  T* out = sig + (long long)rhs * 3 * g.field + pc;
-  out[0] = l * div + T(2) * m * u_x;
-  out[g.field] = l * div + T(2) * m * v_y;
-  out[2 * g.field] = m * (u_y + v_x);
+  T* out = sig + (long long)rhs * 3 * g.field + pc;  // 12 sigma, as the interior tiles store it
+  out[0] = T(12) * (l * div + T(2) * m * u_x);
+  out[g.field] = T(12) * (l * div + T(2) * m * v_y);
+  out[2 * g.field] = T(12) * (m * (u_y + v_x));
 }
 
 template <typename T, int TL_TX, int TL_TY>
@@ -485,10 +493,11 @@ __global__ void __launch_bounds__(TL_TX * TL_TY) sbp_stress2d_tl(Geom g, const T
   }
   __syncthreads();
   const int cx = threadIdx.x + TL_H, cy = threadIdx.y + TL_H;
-  const T u_x = c4(su[0][cy][cx - 2], su[0][cy][cx - 1], su[0][cy][cx + 1], su[0][cy][cx + 2]);
-  const T v_x = c4(su[1][cy][cx - 2], su[1][cy][cx - 1], su[1][cy][cx + 1], su[1][cy][cx + 2]);
-  const T u_y = c4(su[0][cy - 2][cx], su[0][cy - 1][cx], su[0][cy + 1][cx], su[0][cy + 2][cx]);
-  const T v_y = c4(su[1][cy - 2][cx], su[1][cy - 1][cx], su[1][cy + 1][cx], su[1][cy + 2][cx]);
+  // 12 D u and 12 sigma
+  const T u_x = c4u(su[0][cy][cx - 2], su[0][cy][cx - 1], su[0][cy][cx + 1], su[0][cy][cx + 2]);
+  const T v_x = c4u(su[1][cy][cx - 2], su[1][cy][cx - 1], su[1][cy][cx + 1], su[1][cy][cx + 2]);
+  const T u_y = c4u(su[0][cy - 2][cx], su[0][cy - 1][cx], su[0][cy + 1][cx], su[0][cy + 2][cx]);
+  const T v_y = c4u(su[1][cy - 2][cx], su[1][cy - 1][cx], su[1][cy + 1][cx], su[1][cy + 2][cx]);
   const T div = u_x + v_y;
   T* out = sig + (long long)rhs * 3 * g.field + pc;
   out[0] = l * div + T(2) * m * u_x;
@@ -523,7 +532,7 @@ __device__ __forceinline__ void div2d_node(const Geom& g, const WaveFields<T>& f
     ku += inv_h0 * sxy[0];
     kv += inv_h0 * syy[0];
   }
-  const T irh = f.irh2[pc];
+  const T irh = f.irh2[pc] * T(1.0 / 12.0);  // the scratch holds 12 sigma
   const long long p0 = pidx(g, rhs, 0, x, y, 0);
   leapfrog_update<T, MODE, FORCED>(f, p0, f.u_cur[p0], ku * irh, s);
   leapfrog_update<T, MODE, FORCED>(f, p0 + g.field, f.u_cur[p0 + g.field], kv * irh, s);
@@ -565,12 +574,14 @@ __global__ void __launch_bounds__(TL_TX * TL_TY) sbp_div2d_tl(Geom g, WaveFields
   __syncthreads();
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int cx = tx + TL_H, cy = ty + TL_H;
-  const T ku = -c4(sxx[ty][cx - 2], sxx[ty][cx - 1], sxx[ty][cx + 1], sxx[ty][cx + 2]) -
-               c4(sxy[cy - 2][cx], sxy[cy - 1][cx], sxy[cy + 1][cx], sxy[cy + 2][cx]);
-  const T kv = -c4(sxy[cy][cx - 2], sxy[cy][cx - 1], sxy[cy][cx + 1], sxy[cy][cx + 2]) -
-               c4(syy[cy - 2][tx], syy[cy - 1][tx], syy[cy + 1][tx], syy[cy + 2][tx]);
-  leapfrog_update<T, MODE, FORCED>(f, p0, u0, ku * irh, s);
-  leapfrog_update<T, MODE, FORCED>(f, p0 + g.field, u1, kv * irh, s);
+  // 144 D sigma from 12 sigma
+  const T ku = -c4u(sxx[ty][cx - 2], sxx[ty][cx - 1], sxx[ty][cx + 1], sxx[ty][cx + 2]) -
+               c4u(sxy[cy - 2][cx], sxy[cy - 1][cx], sxy[cy + 1][cx], sxy[cy + 2][cx]);
+  const T kv = -c4u(sxy[cy][cx - 2], sxy[cy][cx - 1], sxy[cy][cx + 1], sxy[cy][cx + 2]) -
+               c4u(syy[cy - 2][tx], syy[cy - 1][tx], syy[cy + 1][tx], syy[cy + 2][tx]);
+  const T irs = irh * T(1.0 / 144.0);
+  leapfrog_update<T, MODE, FORCED>(f, p0, u0, ku * irs, s);
+  leapfrog_update<T, MODE, FORCED>(f, p0 + g.field, u1, kv * irs, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -309,7 +309,8 @@ def window_problem(prob: Problem, lo: Sequence[int], hi: Sequence[int]) -> Probl
 
     Sides of the window that are not sides of the domain become Dirichlet
     (their boundary layer is held at zero).  Used to evaluate single entries
-    of a large S apply inside their domain of dependence.
+    of a large S apply inside their domain of dependence.  A mapped problem
+    keeps the node coordinates of the window.
     """
     sl = tuple(slice(lo[a], hi[a] + 1) for a in reversed(range(prob.dim)))
     bc = list(prob.bc)
@@ -323,4 +324,6 @@ def window_problem(prob: Problem, lo: Sequence[int], hi: Sequence[int]) -> Probl
     return Problem(prob.name + "_win", prob.dim, n, prob.h, prob.order, bc, prob.omega,
                    prob.rho[sl].copy(), prob.lam[sl].copy(), prob.mu[sl].copy(),
                    prob.forcing[fsl].copy(), cfl=prob.cfl, periods=prob.periods,
-                   corrected=prob.corrected)
+                   corrected=prob.corrected, implicit=getattr(prob, "implicit", 0),
+                   mapping=None if getattr(prob, "mapping", None) is None
+                   else (prob.mapping[0][sl].copy(), prob.mapping[1][sl].copy()))
