@@ -356,6 +356,60 @@ def threed_measurement(nu, stream, flush):
                             {0: "sbp_stress + sbp_divergence_step (3D)"})
 
 
+def batch_time_to_tol(stream, flush, tol=1e-6):
+    """Time to a relative FP64 residual of ``tol`` for a reduced batch (8
+    shots x 2 frequencies, 0.5 and 1.0 x w10, on layered 128^2 and 192^2: 16
+    systems in 4 members): the batched FP32-stencil / FP64-Krylov solve
+    against the same 16 systems solved one after another by the plain FP64
+    solve.  Contexts are created untimed; each timed region is the solves."""
+    import torch
+    from paper_2205_12344_gb300 import inputs, parallel
+    from paper_2205_12344_gb300.api import WaveHoltz, WaveHoltzBatch
+    nu_list, scales, shots = (128, 192), (0.5, 1.0), 8
+    members = batch_members(nu_list=nu_list, scales=scales, shots=shots)
+    out = {"workload": "8 shots x 2 frequencies (0.5, 1.0 x w10) on layered 128^2/192^2, order 4: 16 systems",
+           "tol": tol}
+    with WaveHoltzBatch(members, "fp32") as wb:
+        wb.solve(tol=tol, maxit=2, raise_on_error=False)          # warm: graphs, autotuner
+        torch.cuda.synchronize()
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xs, infos = wb.solve(tol=tol, maxit=200000, raise_on_error=False)
+        e1.record(stream)
+        e1.synchronize()
+        xb = [x.clone() for x in xs]
+        out["batched"] = {"seconds": e0.elapsed_time(e1) / 1e3, "max_iters": max(i.iters for i in infos),
+                          "max_rel_res": max(i.rel_res for i in infos), "status": max(i.status for i in infos)}
+    seq_s, seq_it, diffs = 0.0, 0, []
+    for m, p in enumerate(members):
+        si = nu_list.index(p.n[0] - 2)
+        xs_pos = parallel.shot_positions((p.n[0] - 1) * 0.01, p.nrhs)
+        sc = scales[m % len(scales)]
+        n1 = xb[m].numel() // p.nrhs
+        for r in range(p.nrhs):
+            q = inputs.cfg_layered_2d(nu=nu_list[si], order=4, nrhs=1, shot_x=[xs_pos[r]], omega_scale=sc)
+            with WaveHoltz(q, precision="fp64") as wh:
+                wh.apply_Pi0()                                   # untimed: autotuner, forced graph
+                torch.cuda.synchronize()
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                x, info = wh.solve(tol=tol, maxit=200000, raise_on_error=False)
+                e1.record(stream)
+                e1.synchronize()
+                seq_s += e0.elapsed_time(e1) / 1e3
+                seq_it = max(seq_it, info.iters)
+                xr = xb[m][r * n1:(r + 1) * n1]
+                diffs.append(float(torch.linalg.norm(xr - x) / torch.linalg.norm(x)))
+    out["sequential_fp64"] = {"seconds": seq_s, "max_iters": seq_it}
+    out["speedup_batched_vs_sequential_fp64"] = seq_s / out["batched"]["seconds"]
+    out["max_solution_rel_diff"] = max(diffs)
+    return out
+
+
 def run_reference(args, ws, rank):
     """--impl reference: the FP64 CPU oracle as it stands, on host cores."""
     if rank != 0:
@@ -476,6 +530,7 @@ def main():
         if not args.no_batch:
             flush.fill_(1.0)
             extra["batch"] = batch_measurement(args.batch_iters, stream)
+            extra["batch"]["time_to_tol"] = batch_time_to_tol(stream, flush)
         if not args.no_mapped:
             extra["mapped"] = mapped_measurement(args.nu, args.mapped_applies, stream, flush)
         if not args.no_3d:
