@@ -69,6 +69,12 @@ __device__ __forceinline__ T sbp_d1(const T* v, long long s, int p, int N) {
   return (v[-2 * s] - T(8) * v[-s] + T(8) * v[s] - v[2 * s]) * T(1.0 / 12.0);
 }
 
+// interior row of the SBP first derivative (unit spacing): (1, -8, 0, 8, -1) / 12
+template <typename T>
+__device__ __forceinline__ T c4(T m2, T m1, T p1, T p2) {
+  return (m2 - T(8) * m1 + T(8) * p1 - p2) * T(1.0 / 12.0);
+}
+
 // Programmatic dependent launch: a step kernel may start while the previous
 // one drains.  Before pdl_wait() a kernel reads only data the solve never
 // writes (lambda, mu, 1/(rho h^2), f/rho); pdl_wait() returns once the previous
@@ -339,6 +345,15 @@ __device__ __forceinline__ int sig_index(int a, int b) {
   return lo == 0 ? (hi == 1 ? 3 : 4) : 5;
 }
 
+// 3D order 4: the 32 x 8 block of this z plane and its 2-node reach lie in
+// rows, columns and planes 4 .. n - 5 (every difference central, every node
+// an unknown): uniform per block, so the fast path never diverges.
+__device__ __forceinline__ bool o4_3d_inner(const Geom& g, int z) {
+  const int x0 = blockIdx.x * blockDim.x, y0 = blockIdx.y * blockDim.y;
+  return x0 >= 4 && x0 + (int)blockDim.x - 1 <= g.n[0] - 5 && y0 >= 4 && y0 + (int)blockDim.y - 1 <= g.n[1] - 5 &&
+         z >= 4 && z <= g.n[2] - 5;
+}
+
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) sbp_stress(Geom g, const T* __restrict__ u, const T* __restrict__ lam,
                                                   const T* __restrict__ mu, T* __restrict__ sig) {
@@ -354,6 +369,30 @@ __global__ void __launch_bounds__(256) sbp_stress(Geom g, const T* __restrict__ 
     rhs = blockIdx.z / nz;
   }
   if (x >= g.n[0] || y >= g.n[1]) return;
+  if (DIM == 3 && o4_3d_inner(g, z)) {  // central differences only, 32-bit offsets from one base
+    const int sy = g.np[0], sz = (int)g.plane;  // neighbour offsets: 2 planes index in 32 bits
+    const long long fld = g.field;
+    const long long pc = pidx(g, 0, 0, x, y, z);
+    const T* U = u + pidx(g, rhs, 0, x, y, z);
+    T gr[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T* b = U + c * fld;
+      gr[c][0] = c4(b[-2], b[-1], b[1], b[2]);
+      gr[c][1] = c4(b[-2 * sy], b[-sy], b[sy], b[2 * sy]);
+      gr[c][2] = c4(b[-2 * sz], b[-sz], b[sz], b[2 * sz]);
+    }
+    const T l = lam[pc], m = mu[pc];
+    const T div = gr[0][0] + gr[1][1] + gr[2][2];
+    T* o = sig + (long long)rhs * 6 * g.field + pc;
+    o[0] = l * div + T(2) * m * gr[0][0];
+    o[fld] = l * div + T(2) * m * gr[1][1];
+    o[2 * fld] = l * div + T(2) * m * gr[2][2];
+    o[3 * fld] = m * (gr[0][1] + gr[1][0]);
+    o[4 * fld] = m * (gr[0][2] + gr[2][0]);
+    o[5 * fld] = m * (gr[1][2] + gr[2][1]);
+    return;
+  }
   const int pos[3] = {x, y, z};
   const long long stride[3] = {1, (long long)g.np[0], g.plane};
   // gradient grad[alpha][a] = D_a u_alpha
@@ -392,6 +431,30 @@ __global__ void __launch_bounds__(256) sbp_divergence_step(Geom g, WaveFields<T>
     z = blockIdx.z % nz;
     rhs = blockIdx.z / nz;
   }
+  if (DIM == 3 && x < g.n[0] && y < g.n[1] && o4_3d_inner(g, z)) {  // central differences, no boundary terms
+    const int sy = g.np[0], sz = (int)g.plane;  // neighbour offsets: 2 planes index in 32 bits
+    const long long fld = g.field;
+    const long long pc = pidx(g, 0, 0, x, y, z);
+    const T* S = f.sigma + (long long)rhs * 6 * g.field + pc;  // planes xx, yy, zz, xy, xz, yz
+    const T* Sxx = S;
+    const T* Syy = S + fld;
+    const T* Szz = S + 2 * fld;
+    const T* Sxy = S + 3 * fld;
+    const T* Sxz = S + 4 * fld;
+    const T* Syz = S + 5 * fld;
+    const T ku = -(c4(Sxx[-2], Sxx[-1], Sxx[1], Sxx[2]) + c4(Sxy[-2 * sy], Sxy[-sy], Sxy[sy], Sxy[2 * sy]) +
+                   c4(Sxz[-2 * sz], Sxz[-sz], Sxz[sz], Sxz[2 * sz]));
+    const T kv = -(c4(Sxy[-2], Sxy[-1], Sxy[1], Sxy[2]) + c4(Syy[-2 * sy], Syy[-sy], Syy[sy], Syy[2 * sy]) +
+                   c4(Syz[-2 * sz], Syz[-sz], Syz[sz], Syz[2 * sz]));
+    const T kw = -(c4(Sxz[-2], Sxz[-1], Sxz[1], Sxz[2]) + c4(Syz[-2 * sy], Syz[-sy], Syz[sy], Syz[2 * sy]) +
+                   c4(Szz[-2 * sz], Szz[-sz], Szz[sz], Szz[2 * sz]));
+    const T irh = f.irh2[pc];
+    const long long p0 = pidx(g, rhs, 0, x, y, z);
+    leapfrog_update<T, MODE, FORCED>(f, p0, f.u_cur[p0], ku * irh, s);
+    leapfrog_update<T, MODE, FORCED>(f, p0 + fld, f.u_cur[p0 + fld], kv * irh, s);
+    leapfrog_update<T, MODE, FORCED>(f, p0 + 2 * fld, f.u_cur[p0 + 2 * fld], kw * irh, s);
+    return;
+  }
   if (!is_unknown(g, x, y, z)) return;
   const int pos[3] = {x, y, z};
   const long long stride[3] = {1, (long long)g.np[0], g.plane};
@@ -424,11 +487,6 @@ __global__ void __launch_bounds__(256) sbp_divergence_step(Geom g, WaveFields<T>
 // run the generic per-node code from global memory.
 // ---------------------------------------------------------------------------
 constexpr int TL_H = 2;
-
-template <typename T>
-__device__ __forceinline__ T c4(T m2, T m1, T p1, T p2) {
-  return (m2 - T(8) * m1 + T(8) * p1 - p2) * T(1.0 / 12.0);
-}
 
 // 12 times the interior difference: the order-4 kernels that carry the
 // operator as 12 D (stresses 12 sigma, divergence 144 D sigma) apply the

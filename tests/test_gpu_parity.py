@@ -260,6 +260,28 @@ def test_layered_1024_fp64_sampled_parity():
     assert np.abs(gv - want).max() <= TOL64 * np.abs(got).max(), (gv, want)
 
 
+@pytest.mark.parametrize("bc,nrhs", [([0, 1, 1, 0, 0, 1], 2), ([1, 1, 1, 1, 1, 1], 1)])
+def test_order4_3d_interior_blocks_match_oracle(bc, nrhs):
+    """A 3D order-4 grid large enough (72 x 24 x 14 nodes) that some 32 x 8
+    blocks and planes lie in rows, columns and planes 4 .. n - 5, so the
+    step kernels' central-difference fast path runs beside the closure path:
+    S, Pi 0 (FP64) and S (FP32) against the oracle."""
+    p = inputs.small_problem(3, [70, 22, 12], 4, bc, seed=23, nrhs=nrhs)
+    assert p.n[0] >= 68 and p.n[1] >= 20 and p.n[2] >= 9   # an interior block exists
+    s = O.build_system(p)
+    v = inputs.random_vectors(p, 1, 24)[0]
+    want = oracle_all_rhs(s, lambda ss, x, r: O.apply_S(ss, x, r), v)
+    want0 = np.concatenate([O.apply_Pi0(s, r) for r in range(p.nrhs)])
+    with _wh(p) as wh:
+        assert rel_err(to_np(wh.apply_S(v)), want) < TOL64
+        assert rel_err(to_np(wh.apply_Pi0()), want0) < TOL64
+        u = inputs.random_vectors(p, 1, 25)[0]
+        kw = oracle_all_rhs(s, lambda ss, x, r: O.minv_K(ss, x), u)
+        assert rel_err(to_np(wh.apply_minvK(u)), kw) < 1e-12
+    with _wh(p, "fp32") as wh:
+        assert rel_err(to_np(wh.apply_S(v)), want) < tol32(s.nt)
+
+
 @pytest.mark.parametrize("variant", ["split", "fused"])
 @pytest.mark.parametrize("shape", [[45, 19], [70, 131]])
 def test_order4_2d_kernel_variants_match_oracle(variant, shape, monkeypatch):
