@@ -770,3 +770,26 @@ def test_mapped_cfl_stable_and_fixed_point():
     assert s.kt * top < 2.0
     v = O.helmholtz_direct(s)
     assert np.linalg.norm(O.apply_Pi(s, v) - v) <= 1e-11 * np.linalg.norm(v)
+
+
+@pytest.mark.parametrize("mapper,bc", [("annulus", [0, 1, 1, 0, 0, 0]), ("wavy", [1, 1, 0, 1, 0, 0])])
+def test_mapped_S_is_M_selfadjoint_with_filter_spectrum(mapper, bc):
+    """On mapped grids (Section 4.1, curvilinear form) the WaveHoltz operator
+    keeps the structure of Sections 3 and 4.5: M(I - S) is symmetric, the
+    eigenvalues of A lie in (0, 3/2), and S acts on each eigenmode of
+    M^{-1}K by sum_n w_n cos(n theta), cos theta = 1 - c dt^2 k2 / 2."""
+    p = inputs.small_problem(2, [9, 8], 4, bc, seed=8)
+    p.mapping = (inputs.annulus_mapping if mapper == "annulus" else inputs.wavy_mapping)(p.n, p.h)
+    s = O.build_system(p)
+    S = O.form_S(s)
+    MA = s.Mdiag[:, None] * (np.eye(S.shape[0]) - S)
+    assert np.abs(MA - MA.T).max() <= 1e-13 * np.abs(MA).max()
+    Ms = np.sqrt(s.Mdiag)
+    ev = np.linalg.eigvalsh(0.5 * (MA + MA.T) / Ms[:, None] / Ms[None, :])
+    g = _golden_kv("section3_filter.txt")
+    assert ev.min() > g["A_eig_lower"] and ev.max() < g["A_eig_upper"]
+    kap = np.linalg.eigvalsh(s.K.toarray() / Ms[:, None] / Ms[None, :])
+    theta = np.arccos(1.0 - s.kt * kap / 2.0)
+    pred = np.sort(np.cos(np.outer(theta, np.arange(len(s.weights)))) @ s.weights)
+    got = np.sort(np.linalg.eigvals(S).real)
+    assert np.abs(pred - got).max() < 1e-11
