@@ -258,7 +258,9 @@ def small_problem(dim, nu, order, bc, seed=0, nrhs=1, omega=None, h=None):
 def annulus_mapping(n, h, span=math.pi / 3, r0=1.0, dr=0.5):
     """Node coordinates (x, y), each of full_shape(n), of an annular sector: the
     radius r0 + dr q' along q and the angle span r' along r (q', r' in [0, 1]
-    over the grid), so the mapping preserves orientation."""
+    over the grid), so the mapping preserves orientation.  The sector's extent
+    is set by r0, dr and span alone; h is taken for the common (n, h)
+    signature of the mapping generators."""
     q = np.arange(n[0]) / (n[0] - 1)
     r = np.arange(n[1]) / (n[1] - 1)
     Q, R = np.meshgrid(q, r)
