@@ -796,6 +796,13 @@ static int step2d_o4_tile(const Geom& g) {
 // One node per thread, global memory (the grid sizes of mapped problems are
 // moderate); the metric planes are (y_r, -x_r, -y_q, x_q).
 // ---------------------------------------------------------------------------
+// The block's nodes and their 2-node reach lie in rows and columns 4 .. n - 5
+// (every difference central, every node an unknown): uniform per block.
+__device__ __forceinline__ bool curv_block_inner(const Geom& g) {
+  const int x0 = blockIdx.x * blockDim.x, y0 = blockIdx.y * blockDim.y;
+  return x0 >= 4 && x0 + (int)blockDim.x - 1 <= g.n[0] - 5 && y0 >= 4 && y0 + (int)blockDim.y - 1 <= g.n[1] - 5;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) curv_stress2d(Geom g, const T* __restrict__ u, const T* __restrict__ lam,
                                                      const T* __restrict__ mu, const T* __restrict__ met,
@@ -810,8 +817,19 @@ __global__ void __launch_bounds__(256) curv_stress2d(Geom g, const T* __restrict
   const long long pc = pidx(g, 0, 0, x, y, 0);
   const T* U = u + pidx(g, rhs, 0, x, y, 0);
   const T* V = U + g.field;
-  const T uq = sbp_d1<T>(U, 1, x, g.n[0]), ur = sbp_d1<T>(U, sy, y, g.n[1]);
-  const T vq = sbp_d1<T>(V, 1, x, g.n[0]), vr = sbp_d1<T>(V, sy, y, g.n[1]);
+  T uq, ur, vq, vr;
+  if (curv_block_inner(g)) {  // central differences, 32-bit offsets
+    const int s1 = g.np[0];
+    uq = c4(U[-2], U[-1], U[1], U[2]);
+    vq = c4(V[-2], V[-1], V[1], V[2]);
+    ur = c4(U[-2 * s1], U[-s1], U[s1], U[2 * s1]);
+    vr = c4(V[-2 * s1], V[-s1], V[s1], V[2 * s1]);
+  } else {
+    uq = sbp_d1<T>(U, 1, x, g.n[0]);
+    ur = sbp_d1<T>(U, sy, y, g.n[1]);
+    vq = sbp_d1<T>(V, 1, x, g.n[0]);
+    vr = sbp_d1<T>(V, sy, y, g.n[1]);
+  }
   const T a0 = met[pc], a1 = met[g.field + pc], a2 = met[2 * g.field + pc], a3 = met[3 * g.field + pc];
   const T u_x = a0 * uq + a2 * ur, u_y = a1 * uq + a3 * ur;  // J times the physical gradient
   const T v_x = a0 * vq + a2 * vr, v_y = a1 * vq + a3 * vr;
@@ -839,6 +857,16 @@ __global__ void __launch_bounds__(256) curv_div2d(Geom g, WaveFields<T> f, StepS
   const T* fru = fqu + g.field;
   const T* fqv = fqu + 2 * g.field;
   const T* frv = fqu + 3 * g.field;
+  if (curv_block_inner(g)) {  // central differences, no boundary terms
+    const int s1 = g.np[0];
+    const T ku = -c4(fqu[-2], fqu[-1], fqu[1], fqu[2]) - c4(fru[-2 * s1], fru[-s1], fru[s1], fru[2 * s1]);
+    const T kv = -c4(fqv[-2], fqv[-1], fqv[1], fqv[2]) - c4(frv[-2 * s1], frv[-s1], frv[s1], frv[2 * s1]);
+    const T irh = f.irh2[pc];
+    const long long p0 = pidx(g, rhs, 0, x, y, 0);
+    leapfrog_update<T, MODE, FORCED>(f, p0, f.u_cur[p0], ku * irh, s);
+    leapfrog_update<T, MODE, FORCED>(f, p0 + g.field, f.u_cur[p0 + g.field], kv * irh, s);
+    return;
+  }
   T ku = -sbp_d1<T>(fqu, 1, x, g.n[0]) - sbp_d1<T>(fru, sy, y, g.n[1]);
   T kv = -sbp_d1<T>(fqv, 1, x, g.n[0]) - sbp_d1<T>(frv, sy, y, g.n[1]);
   const T inv_h0 = T(48.0 / 17.0);
