@@ -793,3 +793,25 @@ def test_mapped_S_is_M_selfadjoint_with_filter_spectrum(mapper, bc):
     pred = np.sort(np.cos(np.outer(theta, np.arange(len(s.weights)))) @ s.weights)
     got = np.sort(np.linalg.eigvals(S).real)
     assert np.abs(pred - got).max() < 1e-11
+
+
+@pytest.mark.parametrize("variant", ["periods2", "implicit", "uncorrected_implicit"])
+def test_mapped_fixed_point_with_other_forms(variant):
+    """The mapped operator composes with the other forms of the method: with
+    the K = 2 filter (Section 3, many-periods filter) and with the implicit
+    time-corrected scheme (Section 4.4) the Helmholtz solution on the sector
+    grid is a fixed point of Pi (with the paper's shifted frequency for the
+    unmodified implicit scheme)."""
+    p = inputs.small_problem(2, [10, 9], 4, [0, 1, 1, 0, 0, 0], seed=12)
+    p.mapping = inputs.annulus_mapping(p.n, p.h)
+    nt = 0
+    if variant == "periods2":
+        p.periods = 2
+    else:
+        p.implicit = 1
+        nt = 8
+        if variant == "uncorrected_implicit":
+            p.corrected = 0
+    s = O.build_system(p, nt=nt) if nt else O.build_system(p)
+    v = O.helmholtz_direct(s)
+    assert np.linalg.norm(O.apply_Pi(s, v) - v) <= 1e-11 * np.linalg.norm(v)
