@@ -145,7 +145,8 @@ ewh_status ewh_create(const ewh_grid_desc* desc, const double* rho, const double
  * order-4 SBP derivative in q and r, J = x_q y_r - x_r y_q; the operator is the
  * energy form with physical derivatives q_x D_q + r_x D_r (and y alike), the
  * mass rho J H h^2, and dt uses max (lambda + 3 mu)/rho (|grad q|^2 + |grad r|^2)/2.
- * Boundary conditions apply to the sides of the (q, r) square.  The other
+ * Boundary conditions apply to the sides of the (q, r) square; a free side is
+ * traction-free on the curved physical boundary it maps to.  The other
  * arguments are as for ewh_create; the identity mapping gives the Cartesian
  * problem.  Requires dim 2 and order 4 (else EWH_EINVAL) and J > 0 at every
  * node (EWH_EINVAL naming the first node where it fails); EWH_ECUDA when no
