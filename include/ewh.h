@@ -10,9 +10,10 @@
  * u(t) solves rho u_tt = div T(u) - f cos wt (Section 2.1, eq. elastic-time)
  * with u(0) = u0, u_t(0) = 0 and S is Pi with f = 0.
  *
- * Discretisation (Section 4.1 and 4.3): nodes of a Cartesian grid, an
- * energy-conserving symmetric L_h (order 2: compact; order 4: fourth-order
- * summation-by-parts) with diagonal mass M, the time-corrected explicit
+ * Discretisation (Section 4.1 and 4.3): nodes of a Cartesian grid (or, through
+ * ewh_create_mapped, of a curvilinear 2D grid), an energy-conserving symmetric
+ * L_h (order 2: compact; order 4: fourth-order summation-by-parts) with
+ * diagonal mass M, the time-corrected explicit
  * leapfrog of eq. (elastic-time-explicit-corrected) with the Taylor start, and
  * the trapezoidal rule for the filter integral (eq. qoper).
  *
