@@ -506,6 +506,27 @@ def test_window_helper_matches_full_apply():
         assert np.abs(got - want).max() <= 1e-12 * np.abs(full).max()
 
 
+def test_window_helper_matches_full_apply_on_mapped_grid():
+    """The same helper on a curvilinear grid: the window keeps its nodes'
+    coordinates, and its metric terms differ from the full grid's only within
+    4 nodes of the window's own sides, outside the sampled node's domain of
+    dependence."""
+    from _helpers import window_sample
+    p = inputs.cfg_layered_2d(nu=70, order=4)
+    L = (p.n[0] - 1) * p.h
+    p.mapping = inputs.annulus_mapping(p.n, p.h, span=0.5, r0=1.5 * L, dr=L)
+    p.omega *= 4.0                                # few steps -> small windows
+    s = O.build_system(p)
+    v = inputs.random_vectors(p, 1, 33)[0]
+    full = O.apply_S(s, v)
+    idx = inputs.unknown_index(p)
+    nn = p.n_nodes()
+    for node in [(6, p.n[1] - 2), (p.n[0] - 3, 4)]:
+        got = window_sample(p, s.nt, v, node, reach=4)
+        want = np.array([full[c * nn + idx[node[1], node[0]]] for c in range(2)])
+        assert np.abs(got - want).max() <= 1e-12 * np.abs(full).max()
+
+
 def test_conjugate_residual_converges_monotonically():
     """Section 4.5 remark: conjugate residual (M inner product) reaches the
     direct solution and its residual norm never increases (unlike CG's)."""
