@@ -462,16 +462,20 @@ def test_windowed_S_equals_full_S_at_centre():
     """S v at one node depends only on v within (N_t + 2) r nodes: the oracle
     on a window around it gives the full-domain value (used for full-size
     sampled parity)."""
-    p = inputs.cfg_layered_2d(nu=60, order=4)
+    p = inputs.cfg_layered_2d(nu=100, order=4)
+    dtc = O.cfl_dt(2, 4, p.h, p.cfl, p.rho, p.lam, p.mu)
+    p.omega = 2 * math.pi / (5.5 * dtc)               # N_t = 6: a window of radius 32 inside the grid
     s = O.build_system(p)
+    assert s.nt == 6
     v = inputs.random_vectors(p, 1, 3)[0]
     full = O.apply_S(s, v)
     idx = inputs.unknown_index(p)
-    r = 2
+    r = 4                                             # order 4: D^T H D reaches 4 nodes per level
     R = (s.nt + 2) * r
-    cx, cy = 30, 55                                   # near the free top
+    cx, cy = 50, 96                                   # near the free top
     lo = [max(0, cx - R), max(0, cy - R)]
     hi = [min(p.n[0] - 1, cx + R), min(p.n[1] - 1, cy + R)]
+    assert lo[0] > 0 and hi[0] < p.n[0] - 1 and lo[1] > 0     # a true sub-window
     w = inputs.window_problem(p, lo, hi)
     sw = O.build_system(w, nt=s.nt)
     widx = inputs.unknown_index(w)
@@ -494,13 +498,17 @@ def test_window_helper_matches_full_apply():
     a Dirichlet corner (order 4: stencil reach 4)."""
     from _helpers import window_sample
     p = inputs.cfg_layered_2d(nu=70, order=4)
-    p.omega *= 4.0                                # few steps -> small windows
+    dtc = O.cfl_dt(2, 4, p.h, p.cfl, p.rho, p.lam, p.mu)
+    p.omega = 2 * math.pi / (5.5 * dtc)           # N_t = 6: windows of radius 32 < the grid
     s = O.build_system(p)
+    assert s.nt == 6
     v = inputs.random_vectors(p, 1, 31)[0]
     full = O.apply_S(s, v)
     idx = inputs.unknown_index(p)
     nn = p.n_nodes()
     for node in [(6, p.n[1] - 2), (p.n[0] - 3, 4)]:
+        R = (s.nt + 2) * 4
+        assert all(min(p.n[a] - 1, node[a] + R) - max(0, node[a] - R) + 1 < p.n[a] for a in range(2))
         got = window_sample(p, s.nt, v, node, reach=4)
         want = np.array([full[c * nn + idx[node[1], node[0]]] for c in range(2)])
         assert np.abs(got - want).max() <= 1e-12 * np.abs(full).max()
@@ -515,13 +523,17 @@ def test_window_helper_matches_full_apply_on_mapped_grid():
     p = inputs.cfg_layered_2d(nu=70, order=4)
     L = (p.n[0] - 1) * p.h
     p.mapping = inputs.annulus_mapping(p.n, p.h, span=0.5, r0=1.5 * L, dr=L)
-    p.omega *= 4.0                                # few steps -> small windows
+    dtc = O.cfl_dt_mapped(p.n, p.h, p.cfl, p.rho, p.lam, p.mu, *p.mapping)
+    p.omega = 2 * math.pi / (5.5 * dtc)           # N_t = 6: windows of radius 32 < the grid
     s = O.build_system(p)
+    assert s.nt == 6
     v = inputs.random_vectors(p, 1, 33)[0]
     full = O.apply_S(s, v)
     idx = inputs.unknown_index(p)
     nn = p.n_nodes()
     for node in [(6, p.n[1] - 2), (p.n[0] - 3, 4)]:
+        R = (s.nt + 2) * 4
+        assert all(min(p.n[a] - 1, node[a] + R) - max(0, node[a] - R) + 1 < p.n[a] for a in range(2))
         got = window_sample(p, s.nt, v, node, reach=4)
         want = np.array([full[c * nn + idx[node[1], node[0]]] for c in range(2)])
         assert np.abs(got - want).max() <= 1e-12 * np.abs(full).max()
