@@ -109,6 +109,13 @@ typedef struct {
   int kernel_variant[2]; /* step-kernel variant picked by the autotuner for the
                             FP64 / FP32 wave solves (-1 = not picked yet; it is
                             picked on the first solve of that precision) */
+  int resident[8];     /* when the FP32 wave solve runs on chip in one cooperative
+                          launch (2D, order 4, one rhs): its partition -- CTA
+                          shape index, CTAs along x and y, interior block width,
+                          first block width, block height (nodes), threads per
+                          CTA, register node pairs per thread; CTA (cx, cy)
+                          owns x from X0 = cx ? first + (cx-1) width : 0 and
+                          y from cy height.  All -1 otherwise. */
 } ewh_problem_info;
 
 typedef struct {
@@ -232,6 +239,8 @@ typedef struct {
   long long steps[2];    /* leapfrog steps (time levels) those solves covered */
   long long waves[2];    /* number of wave solves */
   long long launches;    /* kernel launches issued (as ewh_kernel_launches) */
+  long long grid_wait_timeouts; /* on-chip wave solves whose grid-barrier wait
+                                   gave up (see ewh_set_grid_wait) */
 } ewh_stats;
 
 /* Fill *out (synchronises the context's stream first). */
@@ -239,6 +248,20 @@ ewh_status ewh_get_stats(ewh_ctx* ctx, ewh_stats* out);
 
 /* Zero the accumulated statistics (the launch counter included). */
 ewh_status ewh_reset_stats(ewh_ctx* ctx);
+
+/* Bound of each grid-barrier wait of the on-chip wave solve (no counterpart in
+ * the paper).  The 2D order-4 FP32 single-rhs solve may run every time level in
+ * one cooperative launch whose CTAs meet at a grid barrier once per level.
+ * Every wait there is bounded: after ns nanoseconds (default 1e9) or 2^22
+ * polls the waiting CTA raises an error flag, every CTA leaves at its next
+ * barrier, and the launch fills its accumulator with NaN (so ewh_apply_S
+ * returns NaN and a solve sees an FP32 breakdown and continues with the FP64
+ * operator).  ns = 0 makes every wait give up at once: a way to exercise that
+ * path without a hung GPU.  The count of launches that gave up is in
+ * ewh_stats.grid_wait_timeouts.  Takes effect for the next launch (the stream
+ * is synchronised first); a no-op on contexts that never run on chip.
+ * Errors: EWH_EINVAL (ns < 0), EWH_ECUDA. */
+ewh_status ewh_set_grid_wait(ewh_ctx* ctx, long long ns);
 
 /* ---- Batches: many independent problems advanced together ----------------
  *
@@ -300,15 +323,19 @@ void ewh_batch_destroy(ewh_batch* b);
  *   out[b] = sum_{c < ncomp} sum_{i < nodes} w[i] * x[b][c][i] * y[b][c][i]
  *
  * for b < nbatch, with x, y laid out [nbatch][ncomp][nodes] like the solver's
- * vectors and w one weight per node (e.g. the mass diagonal).  The sums use the
- * same fixed-order two-pass reduction as ewh_mdot.
+ * vectors and w one weight per node (e.g. the mass diagonal).  The sums are
+ * deterministic (a fixed-order two-pass reduction); above 65536 entries per
+ * member they use at most 64 blocks where ewh_mdot uses more, so the two
+ * agree to rounding, not bit for bit.
  *   x, y, w, out  device pointers; out receives nbatch doubles.
  *   cuda_stream   the stream the two kernels run on (NULL = legacy default).
  * Limits: nbatch <= 128 (EWH_EINVAL beyond, with a message in
  * ewh_last_error(NULL)); nodes, ncomp >= 1.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array: calls that
+ * before any stream capture.  The address is tied to the device's context:
+ * after a cudaDeviceReset the next call looks it up again (so, again, make
+ * that call outside a capture).  All calls share the one array: calls that
  * overlap on the GPU (different streams without ordering) race and may return
  * wrong sums, so order them.  Nothing needs clearing between calls: each call
  * writes every partial sum it reads.  Returns EWH_OK, EWH_EINVAL or

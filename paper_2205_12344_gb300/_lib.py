@@ -26,7 +26,7 @@ class ewh_problem_info(ctypes.Structure):
     _fields_ = [("nt", ctypes.c_int), ("periods", ctypes.c_int), ("dt", ctypes.c_double),
                 ("omega", ctypes.c_double), ("omega_tilde", ctypes.c_double), ("kt", ctypes.c_double),
                 ("nodes", ctypes.c_longlong), ("n_unknowns", ctypes.c_longlong), ("nrhs", ctypes.c_int),
-                ("nu", ctypes.c_int * 3), ("kernel_variant", ctypes.c_int * 2)]
+                ("nu", ctypes.c_int * 3), ("kernel_variant", ctypes.c_int * 2), ("resident", ctypes.c_int * 8)]
 
 
 class ewh_solve_info(ctypes.Structure):
@@ -36,7 +36,8 @@ class ewh_solve_info(ctypes.Structure):
 
 class ewh_stats(ctypes.Structure):
     _fields_ = [("wave_ms", ctypes.c_double * 2), ("steps", ctypes.c_longlong * 2),
-                ("waves", ctypes.c_longlong * 2), ("launches", ctypes.c_longlong)]
+                ("waves", ctypes.c_longlong * 2), ("launches", ctypes.c_longlong),
+                ("grid_wait_timeouts", ctypes.c_longlong)]
 
 
 class ewh_problem(ctypes.Structure):
@@ -67,6 +68,7 @@ SIGNATURES = {
     "ewh_kernel_launches": (ctypes.c_longlong, [_P]),
     "ewh_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ewh_stats)]),
     "ewh_reset_stats": (ctypes.c_int, [_P]),
+    "ewh_set_grid_wait": (ctypes.c_int, [_P, ctypes.c_longlong]),
     "ewh_mdot_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _P, _P]),
     "ewh_batch_create": (ctypes.c_int, [ctypes.POINTER(ewh_problem), ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "ewh_batch_apply_S": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
@@ -239,6 +241,10 @@ def ewh_get_stats(ctx):
 
 def ewh_reset_stats(ctx):
     return _check(load().ewh_reset_stats(ctx), ctx)
+
+
+def ewh_set_grid_wait(ctx, ns):
+    return _check(load().ewh_set_grid_wait(ctx, int(ns)), ctx)
 
 
 def ewh_mdot_noalloc(x, y, w, nodes, ncomp, nbatch, out, stream=None):

@@ -120,6 +120,11 @@ class WaveHoltz:
     def reset_stats(self):
         L.ewh_reset_stats(self.ctx)
 
+    def set_grid_wait(self, ns):
+        """Bound of each grid-barrier wait of the on-chip wave solve, in ns
+        (0: every wait gives up at once)."""
+        L.ewh_set_grid_wait(self.ctx, ns)
+
     def close(self):
         if getattr(self, "ctx", None) is not None:
             self.torch.cuda.synchronize()

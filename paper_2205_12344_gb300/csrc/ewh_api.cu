@@ -108,6 +108,7 @@ struct ewh_ctx {
   double wave_ms[2] = {0, 0};
   long long wave_steps[2] = {0, 0};
   long long wave_count[2] = {0, 0};
+  long long grid_timeouts_base = 0;  // grid-wait give-ups counted before the last ewh_reset_stats
 };
 
 namespace {
@@ -206,7 +207,10 @@ ewh_status build_wave(ewh_ctx* ctx, Wave<T>& w, const double* d_rho, const doubl
     }
     EWH_CU(cudaMalloc(&w.d_cosn, sizeof(double) * N));
     EWH_CU(cudaMalloc(&w.d_wnew, sizeof(double) * N));
-    EWH_CU(alloc_zero(&w.bar, 2, ctx->st));
+    EWH_CU(alloc_zero(&w.bar, RS_BAR_WORDS, ctx->st));
+    const unsigned long long wait_ns = RS_WAIT_NS_DEFAULT;
+    EWH_CU(cudaStreamSynchronize(ctx->st));
+    EWH_CU(cudaMemcpy(w.bar + 2, &wait_ns, sizeof(wait_ns), cudaMemcpyHostToDevice));
     EWH_CU(cudaMemcpy(w.d_cosn, hc.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
     EWH_CU(cudaMemcpy(w.d_wnew, hw.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
     for (int k = 0; k < RS_SHAPES; ++k) w.rplan[k] = plan_resident_o4(g, k);
@@ -1851,6 +1855,24 @@ ewh_status ewh_get_info(const ewh_ctx* ctx, ewh_problem_info* info) {
   for (int a = 0; a < 3; ++a) info->nu[a] = ctx->g.nu[a];
   info->kernel_variant[0] = ctx->w64.variant;
   info->kernel_variant[1] = ctx->w32.variant;
+  for (int k = 0; k < 8; ++k) info->resident[k] = -1;
+  const int v = ctx->w32.variant;
+  if (v >= VARIANT_RESIDENT && v < VARIANT_RESIDENT + RS_SHAPES) {
+    const ResidentPlan& p = ctx->w32.rplan[v - VARIANT_RESIDENT];
+    const int r[8] = {p.shape, p.px, p.py, p.bx, p.ex, p.by, RS_SHAPE_THREADS[p.shape], RS_SHAPE_PAIRS[p.shape]};
+    for (int k = 0; k < 8; ++k) info->resident[k] = r[k];
+  }
+  return EWH_OK;
+}
+
+ewh_status ewh_set_grid_wait(ewh_ctx* ctx, long long ns) {
+  if (!ctx) return EWH_EINVAL;
+  if (ns < 0) return fail(ctx, EWH_EINVAL, "grid wait limit must be >= 0 ns");
+  if (!ctx->w32.bar) return EWH_OK;  // this context never runs the on-chip solve
+  const unsigned long long v = (unsigned long long)ns;
+  if (cudaStreamSynchronize(ctx->st) != cudaSuccess ||
+      cudaMemcpy(ctx->w32.bar + 2, &v, sizeof(v), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(ctx, EWH_ECUDA, "setting the grid wait limit failed");
   return EWH_OK;
 }
 
@@ -2136,6 +2158,13 @@ ewh_status ewh_get_stats(ewh_ctx* ctx, ewh_stats* out) {
     out->waves[k] = ctx->wave_count[k];
   }
   out->launches = ctx->launches;
+  out->grid_wait_timeouts = 0;
+  if (ctx->w32.bar) {
+    unsigned n = 0;
+    if (cudaMemcpy(&n, ctx->w32.bar + 4, sizeof(n), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(ctx, EWH_ECUDA, "reading the grid wait counter failed");
+    out->grid_wait_timeouts = (long long)n - ctx->grid_timeouts_base;
+  }
   return EWH_OK;
 }
 
@@ -2145,6 +2174,12 @@ ewh_status ewh_reset_stats(ewh_ctx* ctx) {
   collect_timing(ctx);
   for (int k = 0; k < 2; ++k) ctx->wave_ms[k] = 0, ctx->wave_steps[k] = 0, ctx->wave_count[k] = 0;
   ctx->launches = 0;
+  if (ctx->w32.bar) {
+    unsigned n = 0;
+    if (cudaMemcpy(&n, ctx->w32.bar + 4, sizeof(n), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(ctx, EWH_ECUDA, "reading the grid wait counter failed");
+    ctx->grid_timeouts_base = (long long)n;
+  }
   return EWH_OK;
 }
 

@@ -172,8 +172,12 @@ struct ResidentIO {
   double kt;            // c dt^2
   double w0;            // trapezoid weight of level 0
   int nsteps;
-  unsigned* bar;        // [2] grid-barrier arrivals and error flag (zeroed by the launcher)
+  unsigned* bar;        // [8]: [0] grid-barrier arrivals and [1] error flag (both zeroed by the
+                        // launcher); [2..3] the barrier-wait limit in ns (u64, 0 = give up at
+                        // once); [4] launches whose wait gave up (never reset by a launch)
 };
+constexpr int RS_BAR_WORDS = 8;
+constexpr unsigned long long RS_WAIT_NS_DEFAULT = 1000000000ull;  // one barrier wait, 1 s
 cudaError_t launch_resident_o4(const Geom& g, const ResidentPlan& p, const ResidentIO& io, cudaStream_t st);
 
 // Message for ewh_last_error(NULL) of calls that have no context.

@@ -354,9 +354,10 @@ cudaError_t launch_fill_mass(const Geom& g, int order, const double* rho_full, d
 // ---------------------------------------------------------------------------
 // Weighted inner products without any allocation (ewh_mdot_noalloc).
 //
-// Same deterministic two-pass reduction as the context's M inner product,
-// but the per-block partial sums live in a file-scope device array instead of
-// context-owned memory, so the call allocates nothing.  Capacity:
+// A deterministic two-pass reduction like the context's M inner product (its
+// own block count, at most NOALLOC_BLOCKS, so for large vectors the rounding
+// differs from ewh_mdot's), with the per-block partial sums in a file-scope
+// device array instead of context-owned memory, so the call allocates nothing.  Capacity:
 // NOALLOC_BLOCKS blocks per batch member, at most NOALLOC_MAX_BATCH members.
 // ---------------------------------------------------------------------------
 constexpr int NOALLOC_BLOCKS = 64;
@@ -393,9 +394,34 @@ __global__ void noalloc_final_kernel(const double* __restrict__ part, int nblk, 
 namespace {
 // Device address of g_noalloc_partials, fetched once per device with that
 // device current (in host code the symbol itself is only a host stand-in).
+// The address belongs to the device's current (primary) context: after a
+// cudaDeviceReset the module may load at another address, so the cached
+// value is tagged with the context it was taken in and looked up again when
+// the current context differs.
 constexpr int MAX_DEVICES = 64;
 double* g_noalloc_ptr[MAX_DEVICES] = {nullptr};
+void* g_noalloc_ctx[MAX_DEVICES] = {nullptr};
 std::mutex g_noalloc_mutex;
+
+// The calling thread's current CUDA context (driver handle), or null when
+// the driver entry point is unavailable.
+void* current_cuda_context() {
+  typedef int (*GetCurrentFn)(void**);
+  static GetCurrentFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<GetCurrentFn>(p);
+    else
+      cudaGetLastError();
+  });
+  void* c = nullptr;
+  if (fn && fn(&c) != 0) c = nullptr;
+  return c;
+}
 }  // namespace
 
 extern "C" ewh_status ewh_mdot_noalloc(const double* x, const double* y, const double* w, long long nodes,
@@ -422,7 +448,8 @@ extern "C" ewh_status ewh_mdot_noalloc(const double* x, const double* y, const d
   double* part = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    void* cur = current_cuda_context();
+    if (!g_noalloc_ptr[dev] || (cur && cur != g_noalloc_ctx[dev])) {
       void* p = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
       if (e != cudaSuccess || !p) {
@@ -431,6 +458,7 @@ extern "C" ewh_status ewh_mdot_noalloc(const double* x, const double* y, const d
         return EWH_ECUDA;
       }
       g_noalloc_ptr[dev] = static_cast<double*>(p);
+      g_noalloc_ctx[dev] = current_cuda_context();
     }
     part = g_noalloc_ptr[dev];
   }

@@ -1240,7 +1240,6 @@ cudaError_t launch_minvK(const Geom& g, int order, const T* u, T* out, const T* 
 // ---------------------------------------------------------------------------
 constexpr int RS_HU = 4;  // u halo
 constexpr int RS_HS = 2;  // stress halo
-constexpr unsigned long long RS_TIMEOUT_NS = 1000000000ull;  // one barrier wait, 1 s
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;
@@ -1263,25 +1262,32 @@ __device__ __forceinline__ void red_release_gpu(unsigned* p, unsigned v) {
 // Split form of the grid barrier: rs_arrive after a __syncthreads that
 // orders the CTA's writes (thread 0 counts the CTA in with a release add);
 // rs_wait polls until `target` CTAs have arrived (each wait bounded: it gives
-// up after RS_TIMEOUT_NS or 2^22 polls, or when another CTA raised the error
-// flag, which it then sees every 256 polls) and ends
-// with a __syncthreads.  Work that needs none of the other CTAs' data goes
-// between the two.
+// up after `lim` ns or 2^22 polls, or when another CTA raised the error flag,
+// which it then sees every 256 polls; a zero limit gives up at once, without
+// polling) and ends with a __syncthreads.  Work that needs none of the other
+// CTAs' data goes between the two.
 __device__ __forceinline__ void rs_arrive(unsigned* bar) {
   if (threadIdx.x == 0) red_release_gpu(bar, 1u);
 }
 
-__device__ __forceinline__ bool rs_wait(unsigned* bar, unsigned target, int* s_ok) {
+// Raise the error flag; the CTA that raises it first counts the launch in
+// bar[4].  Returns 0 (the wait failed).
+__device__ __forceinline__ int rs_give_up(unsigned* bar) {
+  if (atomicExch(bar + 1, 1u) == 0u) atomicAdd(bar + 4, 1u);
+  return 0;
+}
+
+__device__ __forceinline__ bool rs_wait(unsigned* bar, unsigned target, int* s_ok, unsigned long long lim) {
   if (threadIdx.x == 0) {
     int ok = ld_acquire_gpu(bar + 1) == 0u;
+    if (ok && lim == 0ull) ok = rs_give_up(bar);
     const unsigned long long t0 = global_ns();
     for (unsigned spins = 1; ok && ld_acquire_gpu(bar) < target; ++spins) {
       if ((spins & 255u) == 0u) {
         if (ld_acquire_gpu(bar + 1) != 0u) {
           ok = 0;
-        } else if (spins > (1u << 22) || global_ns() - t0 > RS_TIMEOUT_NS) {
-          atomicExch(bar + 1, 1u);
-          ok = 0;
+        } else if (spins > (1u << 22) || global_ns() - t0 > lim) {
+          ok = rs_give_up(bar);
         }
       }
     }
@@ -1537,6 +1543,7 @@ template <int NT, int NP>
 __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShape sh, ResidentIO io) {
   if (g.dim != 2) return;
   __shared__ int s_ok;
+  const unsigned long long wait_ns = *reinterpret_cast<const unsigned long long*>(io.bar + 2);
   const int n0 = g.n[0], n1 = g.n[1];
   const int cx = blockIdx.x % sh.px;
   const int X0 = cx == 0 ? 0 : sh.ex + (cx - 1) * sh.bx, Y0 = (blockIdx.x / sh.px) * sh.by;
@@ -1619,7 +1626,7 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
         rs_stress_pair(io.lam, io.mu, npx, obase, qa + 2 * (pa + pp), qy);
     }
     if (n > 0) {
-      if (!rs_wait(io.bar, (unsigned)n * gridDim.x, &s_ok)) {
+      if (!rs_wait(io.bar, (unsigned)n * gridDim.x, &s_ok, wait_ns)) {
         alive = false;
         break;
       }
