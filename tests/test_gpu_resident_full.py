@@ -219,7 +219,7 @@ def test_grid_wait_gives_up_and_context_recovers(monkeypatch):
     from paper_2205_12344_gb300 import _lib as L
     from paper_2205_12344_gb300.api import WaveHoltz
     monkeypatch.setenv("EWH_STEP2D_O4", "r0")
-    p = inputs.small_problem(2, [129, 37], 4, [D, F, F, D, 0, 0], seed=60)
+    p = inputs.small_problem(2, [40, 34], 4, [D, D, D, F, 0, 0], seed=42)  # M(I - S) definite
     s = O.build_system(p)
     v = inputs.random_vectors(p, 1, 61)[0]
     with WaveHoltz(p, precision="fp32") as wh:
