@@ -498,7 +498,10 @@ class SolveInfo:
 
 
 def mdot(s: System, x, y):
-    return float(np.dot(x * s.Mdiag, y))
+    """The M inner product of eq. (amat_sym), sum_i x_i M_i y_i, rounded once
+    (math.fsum of the products x_i M_i y_i): the value does not depend on the
+    order of summation, so any split of the vectors reproduces it exactly."""
+    return math.fsum(x * s.Mdiag * y)
 
 
 def cg_solve(s: System, tol=1e-8, maxit=10000, x0=None, rhs: int = 0, b=None):
