@@ -343,6 +343,17 @@ void ewh_batch_destroy(ewh_batch* b);
 ewh_status ewh_mdot_noalloc(const double* x, const double* y, const double* w, long long nodes, int ncomp,
                             int nbatch, double* out, void* cuda_stream);
 
+/* Measured FMA throughput of the current GPU in floating-point operations per
+ * second (no counterpart in the paper): the arithmetic roofline of step
+ * kernels that are bound by the CUDA cores rather than by memory.  Every thread
+ * of a grid of 8 blocks of 256 threads per SM runs 8 independent FMA chains
+ * (one FMA = 2 operations) for about 50 ms; the run is timed with CUDA events
+ * on cuda_stream (NULL = legacy default) and synchronised.
+ *   precision  EWH_FP64 or EWH_FP32_STENCIL (FP32).
+ * Errors: EWH_EINVAL (bad precision or null output, message in
+ * ewh_last_error(NULL)), EWH_ECUDA. */
+ewh_status ewh_fma_rate(int precision, double* flops_per_second, void* cuda_stream);
+
 /* ---- Layers of the learned warm start --------------------------------------
  *
  * The paper has no learned component: these entry points serve the warm-start

@@ -72,14 +72,6 @@ def centred_difference(N):
     return C.tocsr()
 
 
-def masked_second_difference(N):
-    """N x N: u_{i-1} - 2 u_i + u_{i+1} at non-boundary nodes, 0 at both ends."""
-    T = sp.lil_matrix((N, N))
-    for i in range(1, N - 1):
-        T[i, i - 1], T[i, i], T[i, i + 1] = 1.0, -2.0, 1.0
-    return T.tocsr()
-
-
 def axis_weight(N, lo, hi):
     """Trapezoid factor of each node along one axis: 1/2 on a free end."""
     m = np.ones(N)

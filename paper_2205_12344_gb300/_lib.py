@@ -69,6 +69,7 @@ SIGNATURES = {
     "ewh_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ewh_stats)]),
     "ewh_reset_stats": (ctypes.c_int, [_P]),
     "ewh_set_grid_wait": (ctypes.c_int, [_P, ctypes.c_longlong]),
+    "ewh_fma_rate": (ctypes.c_int, [ctypes.c_int, _D, _P]),
     "ewh_mdot_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _P, _P]),
     "ewh_batch_create": (ctypes.c_int, [ctypes.POINTER(ewh_problem), ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "ewh_batch_apply_S": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
@@ -245,6 +246,13 @@ def ewh_reset_stats(ctx):
 
 def ewh_set_grid_wait(ctx, ns):
     return _check(load().ewh_set_grid_wait(ctx, int(ns)), ctx)
+
+
+def ewh_fma_rate(precision, stream=None):
+    """Measured FMA throughput (floating-point operations per second)."""
+    out = ctypes.c_double()
+    _check(load().ewh_fma_rate(int(precision), ctypes.byref(out), ctypes.c_void_p(stream) if stream else None))
+    return out.value
 
 
 def ewh_mdot_noalloc(x, y, w, nodes, ncomp, nbatch, out, stream=None):

@@ -50,6 +50,9 @@ struct Wave {
   double* d_wnew = nullptr;
   unsigned* bar = nullptr;
   ResidentPlan rplan[RS_SHAPES];
+  // fused 3D order-4 FP32 step: bulk-tensor maps of u_a / u_b, grid (control
+  // words in bar)
+  ZmPlan zm;
 };
 
 // step-kernel variants of the 2D order-4 FP32 solve beyond the launcher's
@@ -214,6 +217,13 @@ ewh_status build_wave(ewh_ctx* ctx, Wave<T>& w, const double* d_rho, const doubl
     EWH_CU(cudaMemcpy(w.d_cosn, hc.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
     EWH_CU(cudaMemcpy(w.d_wnew, hw.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
     for (int k = 0; k < RS_SHAPES; ++k) w.rplan[k] = plan_resident_o4(g, k);
+  }
+  if (sizeof(T) == 4 && g.dim == 3 && ctx->order == 4 && !g.mapped) {
+    EWH_CU(alloc_zero(&w.bar, RS_BAR_WORDS, ctx->st));
+    const unsigned long long wait_ns = RS_WAIT_NS_DEFAULT;
+    EWH_CU(cudaStreamSynchronize(ctx->st));
+    EWH_CU(cudaMemcpy(w.bar + 2, &wait_ns, sizeof(wait_ns), cudaMemcpyHostToDevice));
+    w.zm = plan_zmarch(g, (const float*)w.u_a, (const float*)w.u_b, w.bar);
   }
   return EWH_OK;
 }
@@ -404,6 +414,7 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
   f.frho = nullptr;
   f.sigma = w.sigma;
   f.met = w.met;
+  f.zm = &w.zm;
   StepScalars sc{ctx->kt, 1.0, 0.0, 0.0};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -490,6 +501,7 @@ cudaError_t enqueue_steps(ewh_ctx* ctx, Wave<T>& w, bool forced, long long* nl) 
   f.frho = forced ? w.frho : nullptr;
   f.sigma = w.sigma;
   f.met = w.met;
+  f.zm = &w.zm;
   f.delta = w.delta;
   f.acc = w.acc;
   const double two_pi = 2.0 * M_PI;
@@ -1324,7 +1336,8 @@ ewh_status validate_desc(const ewh_grid_desc* d, int nrhs) {
       return fail(nullptr, EWH_EINVAL, "n[" + std::to_string(a) + "] must be in [" + std::to_string(minn) + ", 2^20]");
   {  // one padded component must index in 32 bits (the step kernels use int offsets)
     long long cells = 1;
-    for (int a = 0; a < d->dim; ++a) cells *= ((d->n[a] + TILE_ROUND - 1) / TILE_ROUND) * TILE_ROUND + 2 * PAD;
+    for (int a = 0; a < d->dim; ++a)
+      cells *= ((d->n[a] + TILE_ROUND - 1) / TILE_ROUND) * TILE_ROUND + ((d->dim == 3 && a == 0) ? PAD3X : 2 * PAD);
     if (cells >= (1LL << 31)) return fail(nullptr, EWH_EINVAL, "grid too large: a padded component must hold < 2^31 nodes");
   }
   for (int k = 0; k < 2 * d->dim; ++k)
@@ -1631,7 +1644,7 @@ ewh_status create_impl(const ewh_grid_desc* desc, const double* xmap, const doub
   for (int a = 0; a < 3; ++a) {
     if (a < dim) {
       const int rounded = ((g.n[a] + TILE_ROUND - 1) / TILE_ROUND) * TILE_ROUND;
-      g.np[a] = rounded + 2 * PAD;
+      g.np[a] = rounded + ((dim == 3 && a == 0) ? PAD3X : 2 * PAD);
       g.off[a] = g.lo_free[a] ? 0 : 1;
       g.nu[a] = g.n[a] - (g.lo_free[a] ? 0 : 1) - (g.hi_free[a] ? 0 : 1);
     } else {
@@ -1641,6 +1654,7 @@ ewh_status create_impl(const ewh_grid_desc* desc, const double* xmap, const doub
     }
   }
   g.pz = dim == 3 ? PAD : 0;
+  g.padx = dim == 3 ? 8 - g.off[0] : PAD;
   g.plane = (long long)g.np[0] * g.np[1];
   g.field = g.plane * g.np[2];
   g.nodes = (long long)g.nu[0] * g.nu[1] * g.nu[2];

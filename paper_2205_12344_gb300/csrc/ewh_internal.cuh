@@ -10,8 +10,11 @@ namespace ewh {
 // Padding (ghost layers, always zero) around the full node grid of every
 // device field.  Order 4 reads up to 6 nodes beyond a tile; tiles are at most
 // 32 wide and the padded extents are rounded up to a multiple of 32 first.
+// 3D fields pad x by 7 or 8 before and at least 8 after the grid (see
+// Geom::padx), with np[0] = rounded + PAD3X.
 constexpr int PAD = 6;
 constexpr int TILE_ROUND = 32;
+constexpr int PAD3X = 16;
 
 // Geometry of one problem in the padded device layout.
 struct Geom {
@@ -20,6 +23,9 @@ struct Geom {
   int lo_free[3];  // 1 if the low side of the axis is a free surface
   int hi_free[3];
   int np[3];       // padded extents (np[2] = 1 in 2D)
+  int padx;        // padding before x = 0 (2D: PAD; 3D: 8 - off[0], so the first unknown node of
+                   // every row sits at a padded x that is a multiple of 4: 16-byte aligned rows of
+                   // unknown pairs for vector and bulk-tensor access)
   int pz;          // padding along z (PAD in 3D, 0 in 2D)
   long long plane; // np[0] * np[1]
   long long field; // elements of one padded component: plane * np[2]
@@ -31,16 +37,26 @@ struct Geom {
   int mapped;      // 1: curvilinear 2D grid (order 4): fluxes through WaveFields::met
 };
 
+// Boundary closure of the diagonal-norm 2-4 summation-by-parts first
+// derivative (rows 0..3 = the first four nodes of a line, columns 0..5); the
+// last four rows are the negated mirror.  Norm weight of the boundary row:
+// 17/48.
+constexpr double SBP_CLOSURE[4][6] = {{-24.0 / 17, 59.0 / 34, -4.0 / 17, -3.0 / 34, 0.0, 0.0},
+                                      {-0.5, 0.0, 0.5, 0.0, 0.0, 0.0},
+                                      {4.0 / 43, -59.0 / 86, 0.0, 59.0 / 86, -4.0 / 43, 0.0},
+                                      {3.0 / 98, 0.0, -59.0 / 98, 0.0, 32.0 / 49, -4.0 / 49}};
+
 // Number of step-kernel variants worth timing for a geometry/order.
 inline int step_variant_count(int dim, int order) {
   if (dim == 2 && order == 4) return 5;  // split with 4 block shapes, fused
   if (dim == 2 && order == 2) return 3;  // tile heights 8, 4, 16
+  if (dim == 3 && order == 4) return 3;  // stress + divergence pair, fused z-march 32x16 and 32x8 (FP32)
   return 1;
 }
 
 __host__ __device__ inline long long pidx(const Geom& g, int rhs, int comp, int x, int y, int z) {
   return ((long long)(rhs * g.dim + comp)) * g.field +
-         (long long)(z + g.pz) * g.plane + (long long)(y + PAD) * g.np[0] + (x + PAD);
+         (long long)(z + g.pz) * g.plane + (long long)(y + PAD) * g.np[0] + (x + g.padx);
 }
 
 // 1 if full-grid node (x, y, z) is an unknown.
@@ -67,6 +83,24 @@ struct StepScalars {
 
 enum StepMode { STEP_FIRST = 0, STEP_MID = 1, STEP_LAST = 2 };
 
+// Plan of the fused 3D order-4 FP32 z-march step (ewh_zmarch.cu): bulk-tensor
+// maps of both u buffers, the persistent grid and the control words (wait
+// limit in ns at [2..3] as a u64, give-up count at [4]).
+// Shapes: k = 0 tiles of 32 x 16 nodes (one CTA per SM), k = 1 tiles of
+// 32 x 8 (two CTAs per SM).
+constexpr int ZM_MAP_BYTES = 128;
+constexpr int ZM_SHAPES = 2;
+struct ZmPlan {
+  int ok[ZM_SHAPES] = {0, 0};
+  int grid[ZM_SHAPES] = {0, 0};
+  int shx[ZM_SHAPES] = {0, 0};  // tile origins before the first unknown (x, y)
+  int shy[ZM_SHAPES] = {0, 0};
+  const float* u_a = nullptr;  // the buffers the maps describe
+  const float* u_b = nullptr;
+  unsigned* ctl = nullptr;
+  alignas(64) unsigned char tmap[ZM_SHAPES][2][ZM_MAP_BYTES];
+};
+
 // Pointers of one wave solve (padded fields, all right-hand sides).
 template <typename T>
 struct WaveFields {
@@ -80,6 +114,7 @@ struct WaveFields {
   const T* frho;   // f / rho per rhs and component, or nullptr (S apply)
   T* sigma;        // order-4 stress scratch (dim*(dim+1)/2 fields per rhs) or nullptr
   const T* met = nullptr;  // mapped grids: 4 planes (y_r, -x_r, -y_q, x_q) of one padded component
+  const ZmPlan* zm = nullptr;  // 3D order 4, FP32: plan of the fused z-march step (host pointer)
 };
 
 // ---- launchers (ewh_stencil.cu) -------------------------------------------
@@ -179,6 +214,11 @@ struct ResidentIO {
 constexpr int RS_BAR_WORDS = 8;
 constexpr unsigned long long RS_WAIT_NS_DEFAULT = 1000000000ull;  // one barrier wait, 1 s
 cudaError_t launch_resident_o4(const Geom& g, const ResidentPlan& p, const ResidentIO& io, cudaStream_t st);
+
+// ---- fused 3D order-4 FP32 step (ewh_zmarch.cu) ------------------------------
+ZmPlan plan_zmarch(const Geom& g, const float* u_a, const float* u_b, unsigned* ctl);
+cudaError_t launch_zmarch(const Geom& g, const ZmPlan& p, int shape, const WaveFields<float>& f, StepMode mode,
+                          const StepScalars& s, cudaStream_t st);
 
 // Message for ewh_last_error(NULL) of calls that have no context.
 void set_global_error(const std::string& msg);

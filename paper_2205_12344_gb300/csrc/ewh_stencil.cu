@@ -28,19 +28,17 @@
 
 namespace ewh {
 
-// Boundary closure of the diagonal-norm 2-4 SBP first derivative (rows 0..3,
-// columns 0..5); the last four rows are the negated mirror.  Norm weight of
-// the boundary row: 17/48.
-__constant__ double c_sbp_d[4][6] = {
-    {-24.0 / 17, 59.0 / 34, -4.0 / 17, -3.0 / 34, 0.0, 0.0},
-    {-0.5, 0.0, 0.5, 0.0, 0.0, 0.0},
-    {4.0 / 43, -59.0 / 86, 0.0, 59.0 / 86, -4.0 / 43, 0.0},
-    {3.0 / 98, 0.0, -59.0 / 98, 0.0, 32.0 / 49, -4.0 / 49}};
-__constant__ float c_sbp_f[4][6] = {
-    {-24.0f / 17, 59.0f / 34, -4.0f / 17, -3.0f / 34, 0.0f, 0.0f},
-    {-0.5f, 0.0f, 0.5f, 0.0f, 0.0f, 0.0f},
-    {4.0f / 43, -59.0f / 86, 0.0f, 59.0f / 86, -4.0f / 43, 0.0f},
-    {3.0f / 98, 0.0f, -59.0f / 98, 0.0f, 32.0f / 49, -4.0f / 49}};
+// The SBP boundary closure (SBP_CLOSURE) in constant memory.
+#define EWH_SBP_ROW(T, r)                                                                         \
+  {                                                                                               \
+    (T)SBP_CLOSURE[r][0], (T)SBP_CLOSURE[r][1], (T)SBP_CLOSURE[r][2], (T)SBP_CLOSURE[r][3],        \
+        (T)SBP_CLOSURE[r][4], (T)SBP_CLOSURE[r][5]                                                \
+  }
+__constant__ double c_sbp_d[4][6] = {EWH_SBP_ROW(double, 0), EWH_SBP_ROW(double, 1), EWH_SBP_ROW(double, 2),
+                                     EWH_SBP_ROW(double, 3)};
+__constant__ float c_sbp_f[4][6] = {EWH_SBP_ROW(float, 0), EWH_SBP_ROW(float, 1), EWH_SBP_ROW(float, 2),
+                                    EWH_SBP_ROW(float, 3)};
+#undef EWH_SBP_ROW
 
 template <typename T>
 __device__ __forceinline__ T sbp_coef(int r, int j);
@@ -1168,6 +1166,19 @@ static cudaError_t launch_mode(const Geom& g, int order, const WaveFields<T>& f,
                               : launch_split_o4<T, MODE, FORCED, 32, 8>(g, f, s, st);
     if (e != cudaSuccess) return e;
   } else {
+    if constexpr (sizeof(T) == 4 && MODE != 3) {
+      // fused z-march: autotuner variants 1 (32 x 16 tiles) and 2 (32 x 8);
+      // EWH_STEP3D_O4=pair|zm16|zm8 (zm: 32 x 8) overrides it
+      const char* ev = getenv("EWH_STEP3D_O4");
+      int zk = g.variant == 1 ? 0 : (g.variant == 2 ? 1 : -1);
+      if (ev) zk = ev[0] != 'z' ? -1 : (strcmp(ev, "zm16") == 0 ? 0 : 1);
+      if (zk >= 0 && f.zm && f.zm->ok[zk]) {
+        cudaError_t e = launch_zmarch(g, *f.zm, zk, f, (StepMode)MODE, s, st);
+        if (e != cudaSuccess) return e;
+        if (nl) *nl += 1;
+        return cudaGetLastError();
+      }
+    }
     cudaError_t e = launch_k(sbp_stress<T, 3>, grd, blk, st, g, (const T*)f.u_cur, f.lam, f.mu, f.sigma);
     if (e != cudaSuccess) return e;
     e = launch_k(sbp_divergence_step<T, 3, MODE, FORCED>, grd, blk, st, g, f, s);
@@ -1561,7 +1572,7 @@ __global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShap
   const int t = threadIdx.x;
   const int F = (int)g.field;  // < 2^31 (checked at creation)
   const int npx = g.np[0];
-  const int obase = (Y0 + PAD) * npx + X0 + PAD;        // padded offset of block node (0, 0)
+  const int obase = (Y0 + PAD) * npx + X0 + g.padx;     // padded offset of block node (0, 0)
   const int ubase = obase - RS_HU * npx - RS_HU;         // ... of u tile position (0, 0)
   const int ux = wx + 2 * RS_HU, uy = wy + 2 * RS_HU;
   const int sxn = wx + 2 * RS_HS, syn = wy + 2 * RS_HS;

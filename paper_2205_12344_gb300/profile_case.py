@@ -11,7 +11,10 @@ capture of one or two launches stays small.
 
 With ``--mapping annulus`` the same medium sits on a curvilinear grid: the
 (q, r) square mapped onto an annular sector of about the same extent (the
-mapped-grid step kernels of Section 4.1).
+mapped-grid step kernels of Section 4.1).  With ``--grf3d`` the workload is
+the 3D Gaussian-random-field cube instead (``--nu`` nodes per axis, order 4).
+The step kernel is the autotuner's choice unless EWH_STEP2D_O4 /
+EWH_STEP3D_O4 name one.
 """
 from __future__ import annotations
 
@@ -25,6 +28,7 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp32", choices=("fp32", "fp64"))
     ap.add_argument("--applies", type=int, default=2, help="applications of S")
     ap.add_argument("--mapping", default="none", choices=("none", "annulus"), help="curvilinear grid")
+    ap.add_argument("--grf3d", action="store_true", help="3D random-field cube instead of the layered 2D medium")
     a = ap.parse_args(argv)
 
     import torch
@@ -32,8 +36,11 @@ def main(argv=None):
     from . import inputs
     from .api import WaveHoltz
 
-    p = inputs.cfg_layered_2d(nu=a.nu, order=4, nrhs=a.nrhs, shot_x=[2.0 + 1.5 * k for k in range(a.nrhs)])
-    if a.mapping == "annulus":
+    if a.grf3d:
+        p = inputs.cfg_grf_3d(nu=a.nu, order=4)
+    else:
+        p = inputs.cfg_layered_2d(nu=a.nu, order=4, nrhs=a.nrhs, shot_x=[2.0 + 1.5 * k for k in range(a.nrhs)])
+    if a.mapping == "annulus" and not a.grf3d:
         L = (p.n[0] - 1) * p.h
         p.mapping = inputs.annulus_mapping(p.n, p.h, span=0.5, r0=1.5 * L, dr=L)
     with WaveHoltz(p, precision=a.precision) as wh:
@@ -44,7 +51,10 @@ def main(argv=None):
             o = wh.apply_S(v)
         torch.cuda.synchronize()
         info = wh.stats()
-        print("applies %d  |S v| %.6e  launches %d" % (a.applies, float(o.norm()), int(info.launches)))
+        k = 0 if a.precision == "fp64" else 1
+        print("applies %d  |S v| %.6e  launches %d  nt %d  ms/level %.4f" %
+              (a.applies, float(o.norm()), int(info.launches), int(wh.info.nt),
+               info.wave_ms[k] / max(info.steps[k], 1)))
 
 
 if __name__ == "__main__":

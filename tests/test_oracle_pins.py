@@ -848,3 +848,54 @@ def test_mapped_fixed_point_with_other_forms(variant):
     s = O.build_system(p, nt=nt) if nt else O.build_system(p)
     v = O.helmholtz_direct(s)
     assert np.linalg.norm(O.apply_Pi(s, v) - v) <= 1e-11 * np.linalg.norm(v)
+
+
+def test_mapped_mms_rate_with_traction_free_curved_side():
+    """Manufactured solution on an annular sector whose outer arc is traction
+    free (Section 4.1, curvilinear form; the free side is the natural
+    boundary condition of the mapped energy).  In polar coordinates
+    u = (r - R0)(r - R1)^2 [sin(pi th / Th) e_r + sin(2 pi th / Th) e_th / 2]
+    vanishes on the inner arc and both radial sides, and its stresses vanish
+    on the outer arc r = R1 (the double zero removes both u and its radial
+    derivative there), so it solves rho w^2 u + div T(u) = f with exactly the
+    discrete problem's boundary conditions.  The discrete Helmholtz solution
+    converges to it at third order or better (fourth-order interior, SBP
+    closure and metric terms of second order at the sides)."""
+    sy = pytest.importorskip("sympy")
+    X, Y = sy.symbols("x y")
+    R0, R1, Th, lam0, mu0, rho0, omega = 1.0, 1.5, math.pi / 3, 2.0, 1.0, 1.0, 1.3
+    r = sy.sqrt(X ** 2 + Y ** 2)
+    th = sy.atan2(Y, X)
+    g = (r - R0) * (r - R1) ** 2
+    ur, ut = g * sy.sin(sy.pi * th / Th), g * sy.sin(2 * sy.pi * th / Th) / 2
+    uex = ur * sy.cos(th) - ut * sy.sin(th)
+    vex = ur * sy.sin(th) + ut * sy.cos(th)
+    ux, uy, vx, vy = sy.diff(uex, X), sy.diff(uex, Y), sy.diff(vex, X), sy.diff(vex, Y)
+    sxx = lam0 * (ux + vy) + 2 * mu0 * ux
+    syy = lam0 * (ux + vy) + 2 * mu0 * vy
+    sxy = mu0 * (uy + vx)
+    # the traction on the outer arc vanishes (checked symbolically at a point)
+    nx, ny = sy.cos(th), sy.sin(th)
+    pt = {X: R1 * math.cos(0.4), Y: R1 * math.sin(0.4)}
+    assert abs(float((sxx * nx + sxy * ny).subs(pt))) < 1e-12
+    assert abs(float((sxy * nx + syy * ny).subs(pt))) < 1e-12
+    fx = rho0 * omega ** 2 * uex + sy.diff(sxx, X) + sy.diff(sxy, Y)
+    fy = rho0 * omega ** 2 * vex + sy.diff(sxy, X) + sy.diff(syy, Y)
+    fns = [sy.lambdify((X, Y), e, "numpy") for e in (fx, fy, uex, vex)]
+    errs = []
+    ms = (17, 33, 65)
+    for m in ms:
+        n = [m, m]
+        h = 1.0 / (m - 1)
+        Xg, Yg = _annulus(n, h, span=Th, r0=R0, dr=R1 - R0)
+        ones = np.ones((m, m))
+        ev = [np.asarray(f(Xg, Yg), dtype=float) for f in fns]
+        prob = inputs.Problem("mms_sector", 2, n, h, 4, [0, 1, 0, 0, 0, 0], omega, rho0 * ones, lam0 * ones,
+                              mu0 * ones, np.stack([np.stack([ev[0], ev[1]])]))
+        prob.mapping = (Xg, Yg)
+        s = O.build_system(prob)
+        vnum = O.helmholtz_direct(s)
+        ex = np.concatenate([ev[2].reshape(-1)[s.sel], ev[3].reshape(-1)[s.sel]])
+        errs.append(np.abs(vnum - ex).max())
+    rates = [math.log(errs[i] / errs[i + 1]) / math.log((ms[i + 1] - 1) / (ms[i] - 1)) for i in range(2)]
+    assert rates[-1] > 2.7, (errs, rates)
