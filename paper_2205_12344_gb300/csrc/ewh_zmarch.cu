@@ -56,6 +56,7 @@ constexpr int ZM_RU = 8;     // u plane ring
 constexpr int ZM_RS = 8;     // (xz, yz, zz) stress ring of the own nodes
 constexpr int ZM_RP = 6;     // pending in-plane divergence ring
 constexpr int ZM_PREF = 2;   // u planes requested ahead of the march
+constexpr int ZM_CLASSES = 9;  // SBP rows of a line position (see ZmScalars)
 
 static_assert(SBP_CLOSURE[0][4] == 0.0 && SBP_CLOSURE[0][5] == 0.0 && SBP_CLOSURE[1][1] == 0.0 &&
                   SBP_CLOSURE[1][3] == 0.0 && SBP_CLOSURE[1][4] == 0.0 && SBP_CLOSURE[1][5] == 0.0 &&
@@ -76,11 +77,13 @@ struct ZmLayout {
   static constexpr int OFF_PD = OFF_SZ + ZM_RS * 3 * OWN;
   static constexpr int OFF_SIP = OFF_PD + ZM_RP * 3 * OWN;
   static constexpr int OFF_TAB = OFF_SIP + 5 * SPLANE;
-  static constexpr int FLOATS = OFF_TAB + 24;  // even: the mbarriers follow, 8-byte aligned
+  static constexpr int OFF_CLS = OFF_TAB + 24;              // tap offsets (int) then weights, per class
+  static constexpr int FLOATS = OFF_CLS + 8 * ZM_CLASSES;   // even: the mbarriers follow, 8-byte aligned
   static constexpr size_t BYTES = 128 + sizeof(float) * FLOATS + sizeof(uint64_t) * ZM_RU;
   static constexpr unsigned TX_BYTES = sizeof(float) * USLOT;  // one bulk-tensor box
   static_assert(USLOT % 32 == 0, "u ring slots stay 128-byte aligned");
   static_assert(FLOATS % 2 == 0, "mbarrier alignment");
+  static_assert(OFF_CLS % 4 == 0, "16-byte table rows");
 };
 
 struct ZmScalars {
@@ -90,6 +93,11 @@ struct ZmScalars {
   float fcos144;    // 144 cos(w t_n)
   float bt12;       // 12 * 48 / 17: the boundary term H^{-1} B in the scaled arithmetic
   int shx, shy;     // tile origins: off[a] - sh + tile size * k (see zm_shift)
+  // 12 D at a node of class k as four taps: offsets toff[4 k ..] and weights
+  // tcf[4 k ..] (classes 0..3: SBP rows 0..3 from the low side, 4: interior,
+  // 5..8: rows 0..3 from the high side; zero weights pad the short rows)
+  int toff[4 * ZM_CLASSES];
+  float tcf[4 * ZM_CLASSES];
 };
 
 // ---- PTX helpers: shared-memory addresses, mbarriers, bulk tensor copies --
@@ -232,6 +240,23 @@ __device__ __forceinline__ float zm_closure12(F v, int p, int n, const float* ta
 
 __device__ __forceinline__ bool zm_closure_row(int p, int n) { return p < 4 || p > n - 5; }
 
+// Class of line position p (0 <= p < n): 0..3 low SBP rows, 4 interior (also
+// used outside the line, where the result is discarded), 5..8 high rows.
+__device__ __forceinline__ int zm_class(int p, int n) {
+  if (p < 0 || p >= n) return 4;
+  if (p < 4) return p;
+  if (p > n - 5) return 5 + (n - 1 - p);
+  return 4;
+}
+
+// 12 D at a node of class c from the four taps of the table (v at the node,
+// `stride` between line neighbours): the same code for every lane.
+__device__ __forceinline__ float zm_d12t(const float* v, int stride, int c, const int* toff, const float* tcf) {
+  const int4 o = *reinterpret_cast<const int4*>(toff + 4 * c);
+  const float4 w = *reinterpret_cast<const float4*>(tcf + 4 * c);
+  return w.x * v[o.x * stride] + w.y * v[o.y * stride] + w.z * v[o.z * stride] + w.w * v[o.w * stride];
+}
+
 // Every thread owns one pair of the stress tile (18 pairs x TY + 4 rows);
 // the threads whose pair lies in the own tile also update those two nodes.
 template <int TY>
@@ -242,14 +267,20 @@ __global__ void __launch_bounds__(zm_threads<TY>(), TY <= 8 ? 2 : 1)
     step3d_o4_zm(Geom g, WaveFields<float> f, ZmScalars sc, unsigned* ctl, const __grid_constant__ CUtensorMap tmu) {
   using L = ZmLayout<TY>;
   extern __shared__ unsigned char zm_raw[];
-  float* const sm = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(zm_raw) + 127) & ~uintptr_t(127));
+  // 128-byte aligned base; offsetting the shared array itself (rather than an
+  // integer round trip) keeps every access below in the shared address space
+  float* const sm = reinterpret_cast<float*>(zm_raw + ((128u - (smem_u32(zm_raw) & 127u)) & 127u));
   uint64_t* const bar = reinterpret_cast<uint64_t*>(sm + L::FLOATS);
   float* const tab = sm + L::OFF_TAB;
   float* const sip = sm + L::OFF_SIP;
   const int t = threadIdx.x;
-  if (t == 0) {  // static indices: the parameter array stays in the constant bank
+  int* const toff = reinterpret_cast<int*>(sm + L::OFF_CLS);
+  float* const tcf = sm + L::OFF_CLS + 4 * ZM_CLASSES;
+  if (t == 0) {  // static indices: the parameter arrays stay in the constant bank
 #pragma unroll
     for (int k = 0; k < 24; ++k) tab[k] = sc.tab12[k];
+#pragma unroll
+    for (int k = 0; k < 4 * ZM_CLASSES; ++k) toff[k] = sc.toff[k], tcf[k] = sc.tcf[k];
     for (int k = 0; k < ZM_RU; ++k) mbar_init(bar + k, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -301,7 +332,10 @@ __global__ void __launch_bounds__(zm_threads<TY>(), TY <= 8 ? 2 : 1)
     const int sx = X0 - 2 + 2 * pi, sy = Y0 - 2 + ri;
     const bool syin = sy >= 0 && sy < n1;
     const bool sg0 = syin && sx >= 0 && sx < n0, sg1 = syin && sx + 1 >= 0 && sx + 1 < n0;
-    const bool sxc0 = zm_closure_row(sx, n0), sxc1 = zm_closure_row(sx + 1, n0), syc = zm_closure_row(sy, n1);
+    const int cx0 = zm_class(sx, n0), cx1 = zm_class(sx + 1, n0), cy0 = zm_class(sy, n1);
+    // warps with a lane on an SBP closure row redo that axis with the class taps
+    const unsigned am = __activemask();
+    const bool wx = __any_sync(am, cx0 != 4 || cx1 != 4), wy = __any_sync(am, cy0 != 4);
     // own pair: nodes (ox, ox + 1), row oy
     const int ox = sx, oy = sy;
     const bool ov0 = own && zm_unknown_x(g, ox) && zm_unknown_y(g, oy);
@@ -376,27 +410,22 @@ __global__ void __launch_bounds__(zm_threads<TY>(), TY <= 8 ? 2 : 1)
                                     tab);
           }
         }
-        // closure rows along x and y (nodes within 4 of a side): replace those differences
-        if (sg0 && sxc0) {
+        // closure rows along x and y (nodes within 4 of a side): the warps that hold
+        // one redo that axis for every lane with the taps of each lane's class
+        if (wx) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const float* Uc = U0 + c * L::UPLANE + ly * ZM_UX + lx;
-            d0[c][0] = zm_closure12([&](int k) { return Uc[k]; }, sx, n0, tab);
+            d0[c][0] = zm_d12t(Uc, 1, cx0, toff, tcf);
+            d1[c][0] = zm_d12t(Uc + 1, 1, cx1, toff, tcf);
           }
         }
-        if (sg1 && sxc1) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float* Uc = U0 + c * L::UPLANE + ly * ZM_UX + lx + 1;
-            d1[c][0] = zm_closure12([&](int k) { return Uc[k]; }, sx + 1, n0, tab);
-          }
-        }
-        if (syin && syc) {
+        if (wy) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const float* Uc = U0 + c * L::UPLANE + ly * ZM_UX + lx;
-            if (sg0) d0[c][1] = zm_closure12([&](int k) { return Uc[k * ZM_UX]; }, sy, n1, tab);
-            if (sg1) d1[c][1] = zm_closure12([&](int k) { return Uc[k * ZM_UX + 1]; }, sy, n1, tab);
+            d0[c][1] = zm_d12t(Uc, ZM_UX, cy0, toff, tcf);
+            d1[c][1] = zm_d12t(Uc + 1, ZM_UX, cy0, toff, tcf);
           }
         }
         float s0[6], s1[6];
@@ -451,33 +480,28 @@ __global__ void __launch_bounds__(zm_threads<TY>(), TY <= 8 ? 2 : 1)
             k0[c] = -(kx0[c] + ky0[c]);
             k1[c] = -(kx1[c] + ky1[c]);
           }
-          if ((ov0 && sxc0) || (ov1 && sxc1) || syc) {
+          if (wx || wy) {
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-              const bool ov = e ? ov1 : ov0;
-              const bool xc = e ? sxc1 : sxc0;
-              const int xe = ox + e;
-              if (!ov || !(xc || syc)) continue;
-#pragma unroll
-              for (int c = 0; c < 3; ++c) {
-                const float* Sx = sip + CX[c] * L::SPLANE + ps + e;
-                const float* Sy = sip + CY[c] * L::SPLANE + ps + e;
-                float kx = e ? kx1[c] : kx0[c], ky = e ? ky1[c] : ky0[c];
-                float bterm = 0.f;
-                if (xc) {
-                  kx = zm_closure12([&](int o) { return Sx[o]; }, xe, n0, tab);
-                  if (xe == 0) bterm -= BT * Sx[0];
-                  else if (xe == n0 - 1) bterm += BT * Sx[0];
-                }
-                if (syc) {
-                  ky = zm_closure12([&](int o) { return Sy[o * ZM_SX]; }, oy, n1, tab);
-                  if (oy == 0) bterm -= BT * Sy[0];
-                  else if (oy == n1 - 1) bterm += BT * Sy[0];
-                }
-                const float kc = -(kx + ky) + bterm;
-                if (e) k1[c] = kc;
-                else k0[c] = kc;
+            for (int c = 0; c < 3; ++c) {
+              const float* Sx = sip + CX[c] * L::SPLANE + ps;
+              const float* Sy = sip + CY[c] * L::SPLANE + ps;
+              if (wx) {
+                kx0[c] = zm_d12t(Sx, 1, cx0, toff, tcf);
+                kx1[c] = zm_d12t(Sx + 1, 1, cx1, toff, tcf);
               }
+              if (wy) {
+                ky0[c] = zm_d12t(Sy, ZM_SX, cy0, toff, tcf);
+                ky1[c] = zm_d12t(Sy + 1, ZM_SX, cy0, toff, tcf);
+              }
+              // boundary terms H^{-1} B sigma on free sides (nodes on the side itself)
+              float b0 = 0.f, b1 = 0.f;
+              if (ox == 0) b0 -= BT * Sx[0];
+              if (ox == n0 - 1) b0 += BT * Sx[0];
+              if (ox + 1 == n0 - 1) b1 += BT * Sx[1];
+              if (oy == 0) b0 -= BT * Sy[0], b1 -= BT * Sy[1];
+              if (oy == n1 - 1) b0 += BT * Sy[0], b1 += BT * Sy[1];
+              k0[c] = -(kx0[c] + ky0[c]) + b0;
+              k1[c] = -(kx1[c] + ky1[c]) + b1;
             }
           }
           float* PD = sm + L::OFF_PD + (zs % ZM_RP) * 3 * L::OWN + r * ZM_TX + 2 * i;
@@ -775,6 +799,29 @@ cudaError_t launch_zmarch(const Geom& g, const ZmPlan& p, int k, const WaveField
   sc.bt12 = (float)(12.0 * 48.0 / 17.0);
   sc.shx = p.shx[k];
   sc.shy = p.shy[k];
+  // four taps per class: the nonzero columns of each closure row (mirrored and
+  // negated from the high side), the interior row, zero-weight padding
+  static const int kCols[4][4] = {{0, 1, 2, 3}, {0, 2, -1, -1}, {0, 1, 3, 4}, {0, 2, 4, 5}};
+  for (int c = 0; c < ZM_CLASSES; ++c)
+    for (int q = 0; q < 4; ++q) {
+      int off = 0;
+      double w = 0.0;
+      if (c == 4) {
+        static const int io[4] = {-2, -1, 1, 2};
+        static const double iw[4] = {1.0, -8.0, 8.0, -1.0};
+        off = io[q];
+        w = iw[q];
+      } else {
+        const int r = c < 4 ? c : c - 5;
+        const int j = kCols[r][q];
+        if (j >= 0) {
+          off = c < 4 ? j - r : r - j;
+          w = (c < 4 ? 12.0 : -12.0) * SBP_CLOSURE[r][j];
+        }
+      }
+      sc.toff[4 * c + q] = off;
+      sc.tcf[4 * c + q] = (float)w;
+    }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(p.grid[k]);
   cfg.blockDim = dim3(k == 0 ? ZmLayout<16>::NT : ZmLayout<8>::NT);
