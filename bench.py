@@ -218,15 +218,22 @@ def cpu_oracle_sample(prob, nt, window_nodes=512, min_seconds=8.0):
 _POOL_SYSTEM = {}
 
 
-def _oracle_pool_init(nu, nt, window_nodes):
+def _oracle_pool_init(nu, nt, window_nodes, kind="layered2d"):
     """Build, once per host process, the oracle system of a window of the
-    layered workload (S applies only: the source plays no part)."""
+    layered 2D workload (by the free top) or of the 3D random-field cube (at
+    its centre); S applies only: the source plays no part."""
     import numpy as np
     from oracle import ewh_oracle as O
     from paper_2205_12344_gb300 import inputs
-    prob = inputs.cfg_layered_2d(nu=nu, order=4)
-    cx, half = prob.n[0] // 2, window_nodes // 2
-    w = inputs.window_problem(prob, [cx - half, prob.n[1] - window_nodes], [cx + half - 1, prob.n[1] - 1])
+    half = window_nodes // 2
+    if kind == "grf3d":
+        prob = inputs.cfg_grf_3d(nu=nu, order=4)
+        c = prob.n[0] // 2
+        w = inputs.window_problem(prob, [c - half] * 3, [c + half - 1] * 3)
+    else:
+        prob = inputs.cfg_layered_2d(nu=nu, order=4)
+        cx = prob.n[0] // 2
+        w = inputs.window_problem(prob, [cx - half, prob.n[1] - window_nodes], [cx + half - 1, prob.n[1] - 1])
     _POOL_SYSTEM["s"] = O.build_system(w, nt=nt)
     _POOL_SYSTEM["v"] = np.random.default_rng(os.getpid()).standard_normal(_POOL_SYSTEM["s"].K.shape[0])
     _POOL_SYSTEM["updates"] = w.n_nodes() * nt
@@ -257,15 +264,16 @@ class OraclePool:
 
     ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
 
-    def __init__(self, nu, nt, window_nodes, workers=None):
+    def __init__(self, nu, nt, window_nodes, workers=None, kind="layered2d"):
         import multiprocessing as mp
         self.workers = workers or len(os.sched_getaffinity(0))
         self.window_nodes = window_nodes
+        self.kind = kind
         saved = {k: os.environ.get(k) for k in self.ENV}
         for k in self.ENV:
             os.environ[k] = "1"
         try:
-            self.pool = mp.get_context("spawn").Pool(self.workers, _oracle_pool_init, (nu, nt, window_nodes))
+            self.pool = mp.get_context("spawn").Pool(self.workers, _oracle_pool_init, (nu, nt, window_nodes, kind))
         finally:
             for k, v in saved.items():
                 if v is None:
@@ -282,8 +290,12 @@ class OraclePool:
         return upd / span / 1e9, span
 
     def describe(self, span):
-        return ("oracle FP64 S apply on %d host processes at once (one core each), each on a %dx%d-node window "
-                "by the free top, %.1f s" % (self.workers, self.window_nodes, self.window_nodes, span))
+        if self.kind == "grf3d":
+            where = "a %d^3-node window at the centre of the cube" % self.window_nodes
+        else:
+            where = "a %dx%d-node window by the free top" % (self.window_nodes, self.window_nodes)
+        return ("oracle FP64 S apply on %d host processes at once (one core each), each on %s, %.1f s" %
+                (self.workers, where, span))
 
     def close(self):
         self.pool.close()
@@ -442,14 +454,86 @@ def mapped_measurement(nu, applies, stream, flush):
 ALG_BYTES_3D = {"fp32": 72.0, "fp64": 144.0}      # read u, u_prev, acc + write u', acc (3 comps) + lambda, mu, 1/M
 
 
-def threed_measurement(nu, stream, flush):
+KERNELS_3D = {0: "sbp_stress + sbp_divergence_step (3D, per level)",
+              1: "step3d_o4_zm<16> (fused z-march, 32x16 tiles, per level)",
+              2: "step3d_o4_zm<8> (fused z-march, 32x8 tiles, per level)"}
+
+
+def threed_measurement(nu, stream, flush, peaks_fma=None, small_nu=48, e2e_iters=5):
     """3D order-4 SBP step on the 256^3 Gaussian-random-field workload (log Vs
-    GRF, Vp = 1.8 Vs, Dirichlet, point source at the centre)."""
+    GRF, Vp = 1.8 Vs, Dirichlet, point source at the centre): S-apply
+    throughput per precision with its roofline (HBM; FP64 also against the
+    measured FP64 FMA rate), the seconds per CG iteration, the end-to-end
+    rate through the C ABI from host buffers, the oracle on every host core,
+    and time to a 1e-6 residual on a reduced cube of the same family."""
+    import numpy as np
+    import torch
+    from paper_2205_12344_gb300 import _lib as L
     from paper_2205_12344_gb300 import inputs
+    from paper_2205_12344_gb300.api import WaveHoltz, make_desc
     prob = inputs.cfg_grf_3d(nu=nu, order=4)
-    return wave_measurement(prob, "grf3d_%d: 3D GRF medium %d^3 unknowns, order-4 SBP, S applies" % (nu, nu),
-                            {"fp32": 2, "fp64": 1}, ALG_BYTES_3D, stream, flush,
-                            {0: "sbp_stress + sbp_divergence_step (3D)"})
+    out = wave_measurement(prob, "grf3d_%d: 3D GRF medium %d^3 unknowns, order-4 SBP, S applies" % (nu, nu),
+                           {"fp32": 2, "fp64": 1}, ALG_BYTES_3D, stream, flush, KERNELS_3D)
+    nodes = out["fp32"]["nodes"]
+    nt = out["fp32"]["nt"]
+    for prec in ("fp32", "fp64"):
+        out[prec]["seconds_per_cg_iteration"] = out[prec]["step_ms"] * nt * 1e-3
+    if peaks_fma:
+        out["fp64"]["alu_roofline"] = alu_roofline(FLOPS_PER_NODE_LEVEL[3], nodes, out["fp64"]["step_ms"],
+                                                   peaks_fma["fp64"], "FP64 3D per-level order-4 pair")
+    # end to end through the C ABI: create from pinned host buffers, a fixed
+    # number of FP32-stencil CG iterations, the solution read into host memory
+    pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(prob, k), dtype=np.float64)).pin_memory()
+           for k in ("rho", "lam", "mu", "forcing")}
+    out_host = torch.empty(prob.nrhs * prob.n_unknowns(), dtype=torch.float64).pin_memory()
+    ms, upd = [], 0
+    for k in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = L.ewh_create(make_desc(prob.dim, prob.n, prob.h, prob.order, prob.bc, L.EWH_FP32_STENCIL, prob.cfl),
+                           pin["rho"], pin["lam"], pin["mu"], prob.omega, pin["forcing"], prob.nrhs,
+                           stream.cuda_stream)
+        L.ewh_solve(ctx, 1e-6, e2e_iters, None, out_host, raise_on_error=False)
+        sts = L.ewh_get_stats(ctx)
+        L.ewh_destroy(ctx)
+        t1 = time.perf_counter()
+        if k > 0:
+            ms.append((t1 - t0) * 1e3)
+            upd += (sts.steps[0] + sts.steps[1]) * nodes
+    out["e2e"] = {"value": upd / (sum(ms) * 1e-3) / 1e9, "unit": UNIT,
+                  "h2d_bytes_per_step": sum(int(pin[k].numel()) * 8 for k in pin),
+                  "d2h_bytes_per_step": int(out_host.numel()) * 8, "ms_per_step": statistics.mean(ms),
+                  "step": "create from host buffers + FP64 Pi 0 + %d FP32-stencil CG iterations + FP64 residual, "
+                          "solution to host" % e2e_iters}
+    # time to 1e-6 on a reduced cube (the 256^3 cube needs O(1e4) iterations)
+    small = inputs.cfg_grf_3d(nu=small_nu, order=4)
+    row = {"workload": "grf3d_%d (same family, %d^3 unknowns), order 4, tol 1e-6" % (small_nu, small_nu)}
+    for prec in ("fp64", "fp32"):
+        with WaveHoltz(small, precision=prec) as wh:
+            wh.apply_S(torch.zeros(wh.n, dtype=torch.float64, device="cuda"))   # untimed: autotuner, graphs
+            torch.cuda.synchronize()
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x, info = wh.solve(tol=1e-6, maxit=20000, raise_on_error=False)
+            e1.record(stream)
+            e1.synchronize()
+            row[prec] = {"seconds": e0.elapsed_time(e1) / 1e3, "iters": info.iters, "rel_res": info.rel_res,
+                         "status": info.status}
+    row["speedup_mixed_vs_fp64"] = row["fp64"]["seconds"] / row["fp32"]["seconds"]
+    out["time_to_tol_reduced"] = row
+    return out
+
+
+def threed_cpu_baseline(nu, nt, window_nodes=32, seconds=8.0):
+    """The oracle's 3D S apply on every host core (a window of the cube)."""
+    pool = OraclePool(nu, nt, window_nodes, kind="grf3d")
+    pool.round(0.5)
+    val, span = pool.round(seconds)
+    desc = pool.describe(span)
+    pool.close()
+    return {"value": val, "unit": UNIT, "cores": pool.workers, "kind": "oracle", "sample": desc}
 
 
 def batch_time_to_tol(stream, flush, tol=1e-6):
@@ -638,7 +722,7 @@ def main():
         if not args.no_mapped:
             extra["mapped"] = mapped_measurement(args.nu, args.mapped_applies, stream, flush)
         if not args.no_3d:
-            extra["grf3d"] = threed_measurement(args.nu3d, stream, flush)
+            extra["grf3d"] = threed_measurement(args.nu3d, stream, flush, peaks_fma)
     wh.close()
 
     # end to end through the C ABI with host buffers: create (H2D of medium and
@@ -675,6 +759,8 @@ def main():
     if rank == 0:
         cpu_val, cpu_desc = cpu_oracle_sample(prob, nt) if ws == 1 else (None, None)
         cpu_all = None
+        if ws == 1 and "grf3d" in extra:
+            extra["grf3d"]["cpu_baseline"] = threed_cpu_baseline(args.nu3d, extra["grf3d"]["fp32"]["nt"])
         if ws == 1:
             pool = OraclePool(args.nu, nt, 512)
             pool.round(0.5)                               # warm: every process has built its window

@@ -43,26 +43,21 @@
 #include <cstring>
 
 #include "ewh_internal.cuh"
+#include "ewh_march.cuh"
 
 namespace ewh {
 
 namespace {
 
 constexpr int ZM_TX = 32;    // own nodes per tile along x
-constexpr int ZM_PX = 16;    // own node pairs per tile row
 constexpr int ZM_UX = 40;    // u tile row: x from X0 - 4 (the bulk-tensor box width)
 constexpr int ZM_SX = 36;    // stress tile row: x from X0 - 2
 constexpr int ZM_RU = 8;     // u plane ring
 constexpr int ZM_RS = 8;     // (xz, yz, zz) stress ring of the own nodes
 constexpr int ZM_RP = 6;     // pending in-plane divergence ring
 constexpr int ZM_PREF = 2;   // u planes requested ahead of the march
-constexpr int ZM_CLASSES = 9;  // SBP rows of a line position (see ZmScalars)
 
-static_assert(SBP_CLOSURE[0][4] == 0.0 && SBP_CLOSURE[0][5] == 0.0 && SBP_CLOSURE[1][1] == 0.0 &&
-                  SBP_CLOSURE[1][3] == 0.0 && SBP_CLOSURE[1][4] == 0.0 && SBP_CLOSURE[1][5] == 0.0 &&
-                  SBP_CLOSURE[2][2] == 0.0 && SBP_CLOSURE[2][5] == 0.0 && SBP_CLOSURE[3][1] == 0.0 &&
-                  SBP_CLOSURE[3][3] == 0.0,
-              "the closure taps below skip exactly the zero entries of the SBP boundary block");
+
 
 template <int TY>
 struct ZmLayout {
@@ -100,68 +95,6 @@ struct ZmScalars {
   float tcf[4 * ZM_CLASSES];
 };
 
-// ---- PTX helpers: shared-memory addresses, mbarriers, bulk tensor copies --
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ unsigned long long zm_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Request one u plane (3 components of box ZM_UX x UY at padded (cx, cy, cz),
-// components cc .. cc + 2) into dst; completion is counted on bar.
-__device__ __forceinline__ void zm_issue(const CUtensorMap* tm, float* dst, uint64_t* bar, int cx, int cy, int cz,
-                                         int cc, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-      "[%6];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(cx), "r"(cy), "r"(cz), "r"(cc), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void zm_pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void zm_pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-// ---- the SBP first derivative, scaled by 12 --------------------------------
-__device__ __forceinline__ float c4u(float m2, float m1, float p1, float p2) { return (m2 - p2) + 8.0f * (p1 - m1); }
-
-// First and last line positions read by the difference at p (line of n >= 8
-// nodes): the exact reach of each row of D (closure rows 0..3 read columns
-// {0,1,2,3}, {0,2}, {0,1,3,4}, {0,2,4,5}; the interior p +- 2).
-__device__ __forceinline__ int zm_lo(int p, int n) {
-  if (p < 4) return 0;
-  if (p > n - 5) {
-    const int r = n - 1 - p;
-    return n - 1 - (r == 0 ? 3 : r == 1 ? 2 : r == 2 ? 4 : 5);
-  }
-  return p - 2;
-}
-__device__ __forceinline__ int zm_hi(int p, int n) {
-  if (p < 4) return p == 0 ? 3 : p == 1 ? 2 : p == 2 ? 4 : 5;
-  if (p > n - 5) return n - 1;
-  return p + 2;
-}
-
-__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
-__device__ __forceinline__ void st2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
-
 // Stresses (scaled by 12) at one node from its nine scaled derivatives
 // d[c][a] = 12 D_a u_c; out: xx, yy, zz, xy, xz, yz.
 __device__ __forceinline__ void zm_sigma(const float d[3][3], float l, float m, float s[6]) {
@@ -179,83 +112,53 @@ struct ZmOperands {  // update operands of one own node pair at one output plane
   float2 d[3], a[3], f[3], irh;
 };
 
+// Offset of node (x, y) of plane 0 in one padded component (32 bits: a
+// component holds fewer than 2^31 nodes); plane z adds z * Geom::plane.
+__device__ __forceinline__ int zm_off(const Geom& g, int x, int y) {
+  return g.pz * (int)g.plane + (y + PAD) * g.np[0] + x + g.padx;
+}
+
+// Update operands of the own pair at component offset o (node pair o, o + 1;
+// v0, v1: which of them are unknowns); D, A, R: delta, acc and f/rho of this
+// right-hand side, F the component stride.
 template <bool FORCED>
-__device__ __forceinline__ void zm_load_ops(const Geom& g, const WaveFields<float>& f, int rhs, int x, int y, int z,
-                                            bool v0, bool v1, ZmOperands& op) {
-  const long long p = pidx(g, rhs, 0, x, y, z);
-  const long long pc = pidx(g, 0, 0, x, y, z);
-  const long long F = g.field;
+__device__ __forceinline__ void zm_load_ops(const float* D, const float* A, const float* R, const float* irh2, int o,
+                                            int F, bool v0, bool v1, ZmOperands& op) {
   if (v0 && v1) {  // 8-byte aligned: x - off[0] and the padded row start are even
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      op.d[c] = __ldcs(reinterpret_cast<const float2*>(f.delta + p + c * F));
-      op.a[c] = __ldcs(reinterpret_cast<const float2*>(f.acc + p + c * F));
-      if (FORCED) op.f[c] = __ldg(reinterpret_cast<const float2*>(f.frho + p + c * F));
+      op.d[c] = __ldcs(reinterpret_cast<const float2*>(D + o + c * F));
+      op.a[c] = __ldcs(reinterpret_cast<const float2*>(A + o + c * F));
+      if (FORCED) op.f[c] = __ldg(reinterpret_cast<const float2*>(R + o + c * F));
     }
-    op.irh = __ldg(reinterpret_cast<const float2*>(f.irh2 + pc));
+    op.irh = __ldg(reinterpret_cast<const float2*>(irh2 + o));
   } else {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      op.d[c] = make_float2(v0 ? f.delta[p + c * F] : 0.f, v1 ? f.delta[p + c * F + 1] : 0.f);
-      op.a[c] = make_float2(v0 ? f.acc[p + c * F] : 0.f, v1 ? f.acc[p + c * F + 1] : 0.f);
-      if (FORCED) op.f[c] = make_float2(v0 ? f.frho[p + c * F] : 0.f, v1 ? f.frho[p + c * F + 1] : 0.f);
+      op.d[c] = make_float2(v0 ? D[o + c * F] : 0.f, v1 ? D[o + c * F + 1] : 0.f);
+      op.a[c] = make_float2(v0 ? A[o + c * F] : 0.f, v1 ? A[o + c * F + 1] : 0.f);
+      if (FORCED) op.f[c] = make_float2(v0 ? R[o + c * F] : 0.f, v1 ? R[o + c * F + 1] : 0.f);
     }
-    op.irh = make_float2(v0 ? f.irh2[pc] : 0.f, v1 ? f.irh2[pc + 1] : 0.f);
+    op.irh = make_float2(v0 ? irh2[o] : 0.f, v1 ? irh2[o + 1] : 0.f);
   }
 }
 
-// lambda, mu at the node pair (x, x + 1), row y, plane z (zero outside the grid)
-__device__ __forceinline__ void zm_load_lm(const Geom& g, const WaveFields<float>& f, int x, int y, int z, bool use,
-                                           float2& l, float2& m) {
-  l = m = make_float2(0.f, 0.f);
-  if (!use || y < 0 || y >= g.n[1]) return;
-  const long long pc = pidx(g, 0, 0, x, y, z);
-  if (x >= 0 && x + 1 < g.n[0]) {  // padded x even: 8-byte aligned
-    l = __ldg(reinterpret_cast<const float2*>(f.lam + pc));
-    m = __ldg(reinterpret_cast<const float2*>(f.mu + pc));
+// lambda, mu at the stress pair at component offset o (zero outside the grid;
+// g0, g1: which nodes lie in it)
+__device__ __forceinline__ void zm_load_lm(const float* lam, const float* mu, int o, bool g0, bool g1, float2& l,
+                                           float2& m) {
+  if (g0 && g1) {  // padded x even: 8-byte aligned
+    l = __ldg(reinterpret_cast<const float2*>(lam + o));
+    m = __ldg(reinterpret_cast<const float2*>(mu + o));
     return;
   }
-  if (x >= 0 && x < g.n[0]) l.x = __ldg(f.lam + pc), m.x = __ldg(f.mu + pc);
-  if (x + 1 >= 0 && x + 1 < g.n[0]) l.y = __ldg(f.lam + pc + 1), m.y = __ldg(f.mu + pc + 1);
+  l = m = make_float2(0.f, 0.f);
+  if (g0) l.x = __ldg(lam + o), m.x = __ldg(mu + o);
+  if (g1) l.y = __ldg(lam + o + 1), m.y = __ldg(mu + o + 1);
 }
 
 __device__ __forceinline__ bool zm_unknown_x(const Geom& g, int x) { return x >= g.off[0] && x < g.off[0] + g.nu[0]; }
 __device__ __forceinline__ bool zm_unknown_y(const Geom& g, int y) { return y >= g.off[1] && y < g.off[1] + g.nu[1]; }
-
-// The closure rows of 12 D (p < 4 or p > n - 5); v(o) is the value at offset o.
-template <class F>
-__device__ __forceinline__ float zm_closure12(F v, int p, int n, const float* tab) {
-  const bool low = p < 4;
-  const int r = low ? p : n - 1 - p;
-  auto w = [&](int j) { return low ? v(j - p) : v(n - 1 - j - p); };
-  float d;
-  switch (r) {
-    case 0: d = tab[0] * w(0) + tab[1] * w(1) + tab[2] * w(2) + tab[3] * w(3); break;
-    case 1: d = tab[6] * w(0) + tab[8] * w(2); break;
-    case 2: d = tab[12] * w(0) + tab[13] * w(1) + tab[15] * w(3) + tab[16] * w(4); break;
-    default: d = tab[18] * w(0) + tab[20] * w(2) + tab[22] * w(4) + tab[23] * w(5); break;
-  }
-  return low ? d : -d;
-}
-
-__device__ __forceinline__ bool zm_closure_row(int p, int n) { return p < 4 || p > n - 5; }
-
-// Class of line position p (0 <= p < n): 0..3 low SBP rows, 4 interior (also
-// used outside the line, where the result is discarded), 5..8 high rows.
-__device__ __forceinline__ int zm_class(int p, int n) {
-  if (p < 0 || p >= n) return 4;
-  if (p < 4) return p;
-  if (p > n - 5) return 5 + (n - 1 - p);
-  return 4;
-}
-
-// 12 D at a node of class c from the four taps of the table (v at the node,
-// `stride` between line neighbours): the same code for every lane.
-__device__ __forceinline__ float zm_d12t(const float* v, int stride, int c, const int* toff, const float* tcf) {
-  const int4 o = *reinterpret_cast<const int4*>(toff + 4 * c);
-  const float4 w = *reinterpret_cast<const float4*>(tcf + 4 * c);
-  return w.x * v[o.x * stride] + w.y * v[o.y * stride] + w.z * v[o.z * stride] + w.w * v[o.w * stride];
-}
 
 // Every thread owns one pair of the stress tile (18 pairs x TY + 4 rows);
 // the threads whose pair lies in the own tile also update those two nodes.
@@ -340,18 +243,29 @@ __global__ void __launch_bounds__(zm_threads<TY>(), TY <= 8 ? 2 : 1)
     const int ox = sx, oy = sy;
     const bool ov0 = own && zm_unknown_x(g, ox) && zm_unknown_y(g, oy);
     const bool ov1 = own && zm_unknown_x(g, ox + 1) && zm_unknown_y(g, oy);
+    // component offsets of this thread's pairs at plane 0, and the state of this rhs
+    const int PL = (int)g.plane;
+    const int so = zm_off(g, sx, sy);
+    const long long ro = (long long)rhs * 3 * g.field;
+    const float* const Dr = f.delta + ro;
+    const float* const Ar = f.acc + ro;
+    const float* const Rr = FORCED ? f.frho + ro : nullptr;
+    float* const Dw = f.delta + ro;
+    float* const Aw = f.acc + ro;
+    float* const Uw = f.u_next + ro;
     // lambda, mu of the next stress plane, requested one plane ahead
     float2 lm_l, lm_m;
     int lm_plane = slo;
-    zm_load_lm(g, f, sx, sy, slo, true, lm_l, lm_m);
+    zm_load_lm(f.lam, f.mu, so + slo * PL, sg0, sg1, lm_l, lm_m);
     ZmOperands op;
     int op_plane = -1;
     if (ov0 || ov1) {
-      zm_load_ops<FORCED>(g, f, rhs, ox, oy, za, ov0, ov1, op);
+      zm_load_ops<FORCED>(Dr, Ar, Rr, f.irh2, so + za * PL, F, ov0, ov1, op);
       op_plane = za;
     }
 
     int next_s = slo, next_o = za, jfail = uhi + 1;
+    bool wait_bad = false;
     for (int j = ulo; j <= uhi; ++j) {
       // ---- wait for u plane j (bounded)
       {
@@ -367,18 +281,21 @@ __global__ void __launch_bounds__(zm_threads<TY>(), TY <= 8 ? 2 : 1)
             }
           }
         }
-        if (__syncthreads_or(!ok)) {
-          alive = false;
-          jfail = j;
-          break;
-        }
-        phase ^= 1u << k;
+        // no barrier here: the threads agree on a failed wait at the next one
+        if (ok) phase ^= 1u << k;
+        wait_bad = !ok;
       }
       // ---- stress planes whose u planes have all arrived
-      while (next_s <= shi && max(hs0, zm_hi(next_s, n2)) <= j) {
+      bool any_sigma = false, failed = false;
+      // the last stress plane complete at this step: every u plane its prefix of
+      // stress planes reads has arrived (the prefix maximum of the reach is
+      // max(hs0, hi(zs)), non-decreasing in zs)
+      int s_last = min(shi, j);
+      while (s_last >= next_s && max(hs0, zm_hi(s_last, n2)) > j) --s_last;
+      for (; next_s <= s_last;) {
         const int zs = next_s;
         if (lm_plane != zs) {
-          zm_load_lm(g, f, sx, sy, zs, true, lm_l, lm_m);
+          zm_load_lm(f.lam, f.mu, so + zs * PL, sg0, sg1, lm_l, lm_m);
           lm_plane = zs;
         }
         const float* U0 = sm + (zs & (ZM_RU - 1)) * L::USLOT;
@@ -453,10 +370,14 @@ __global__ void __launch_bounds__(zm_threads<TY>(), TY <= 8 ? 2 : 1)
           st2(SZ + 2 * L::OWN, s0[2], s1[2]);
         }
         if (zs + 1 <= shi) {
-          zm_load_lm(g, f, sx, sy, zs + 1, true, lm_l, lm_m);
+          zm_load_lm(f.lam, f.mu, so + (zs + 1) * PL, sg0, sg1, lm_l, lm_m);
           lm_plane = zs + 1;
         }
-        __syncthreads();  // the stress plane is complete
+        if (__syncthreads_or(wait_bad)) {  // the stress plane is complete (or a wait gave up)
+          failed = true;
+          break;
+        }
+        any_sigma = true;
         if (zs >= za && zs < zb && (ov0 || ov1)) {
           // in-plane part of -D sigma + H^{-1} B sigma at the own pair: central
           // differences, then the closure rows and boundary terms of nodes within 4 of
@@ -509,13 +430,21 @@ __global__ void __launch_bounds__(zm_threads<TY>(), TY <= 8 ? 2 : 1)
           for (int c = 0; c < 3; ++c) st2(PD + c * L::OWN, k0[c], k1[c]);
         }
         ++next_s;
-        if (next_s <= shi && max(hs0, zm_hi(next_s, n2)) <= j) __syncthreads();  // another plane follows
+        if (next_s <= s_last) __syncthreads();  // another plane follows
+      }
+      if (!any_sigma && !failed) failed = __syncthreads_or(wait_bad) != 0;
+      if (failed) {  // a wait gave up: every thread stops here
+        alive = false;
+        jfail = j;
+        break;
       }
       // ---- output planes whose stress planes all exist
-      while (next_o < zb && max(ho0, zm_hi(next_o, n2)) <= next_s - 1) {
+      int o_last = min(zb - 1, next_s - 1);
+      while (o_last >= next_o && max(ho0, zm_hi(o_last, n2)) > next_s - 1) --o_last;
+      for (; next_o <= o_last;) {
         const int zo = next_o;
         if (ov0 || ov1) {
-          if (op_plane != zo) zm_load_ops<FORCED>(g, f, rhs, ox, oy, zo, ov0, ov1, op);
+          if (op_plane != zo) zm_load_ops<FORCED>(Dr, Ar, Rr, f.irh2, so + zo * PL, F, ov0, ov1, op);
           const int po = r * ZM_TX + 2 * i;
           const float* PD = sm + L::OFF_PD + (zo % ZM_RP) * 3 * L::OWN + po;
           float k0[3], k1[3];
@@ -553,7 +482,7 @@ __global__ void __launch_bounds__(zm_threads<TY>(), TY <= 8 ? 2 : 1)
           }
           // leapfrog / filter update of the pair (increment form)
           const float* Uo = sm + (zo & (ZM_RU - 1)) * L::USLOT + (r + 4) * ZM_UX + 4 + 2 * i;
-          const long long p = pidx(g, rhs, 0, ox, oy, zo);
+          const int p = so + zo * PL;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const float2 u = ld2(Uo + c * L::UPLANE);
@@ -579,21 +508,21 @@ __global__ void __launch_bounds__(zm_threads<TY>(), TY <= 8 ? 2 : 1)
               ac0 = op.a[c].x + sc.wnew * un0;
               ac1 = op.a[c].y + sc.wnew * un1;
             }
-            const long long pc = p + (long long)c * F;
+            const int pc = p + c * F;
             if (ov0 && ov1) {
               if (MODE != STEP_LAST) {
-                __stcs(reinterpret_cast<float2*>(f.delta + pc), make_float2(dd0, dd1));
-                __stcs(reinterpret_cast<float2*>(f.u_next + pc), make_float2(un0, un1));
+                __stcs(reinterpret_cast<float2*>(Dw + pc), make_float2(dd0, dd1));
+                __stcs(reinterpret_cast<float2*>(Uw + pc), make_float2(un0, un1));
               }
-              __stcs(reinterpret_cast<float2*>(f.acc + pc), make_float2(ac0, ac1));
+              __stcs(reinterpret_cast<float2*>(Aw + pc), make_float2(ac0, ac1));
             } else {
               if (ov0) {
-                if (MODE != STEP_LAST) f.delta[pc] = dd0, f.u_next[pc] = un0;
-                f.acc[pc] = ac0;
+                if (MODE != STEP_LAST) Dw[pc] = dd0, Uw[pc] = un0;
+                Aw[pc] = ac0;
               }
               if (ov1) {
-                if (MODE != STEP_LAST) f.delta[pc + 1] = dd1, f.u_next[pc + 1] = un1;
-                f.acc[pc + 1] = ac1;
+                if (MODE != STEP_LAST) Dw[pc + 1] = dd1, Uw[pc + 1] = un1;
+                Aw[pc + 1] = ac1;
               }
             }
           }
@@ -602,7 +531,7 @@ __global__ void __launch_bounds__(zm_threads<TY>(), TY <= 8 ? 2 : 1)
       }
       // operands of the next output plane, one plane ahead
       if (next_o < zb && op_plane != next_o && (ov0 || ov1)) {
-        zm_load_ops<FORCED>(g, f, rhs, ox, oy, next_o, ov0, ov1, op);
+        zm_load_ops<FORCED>(Dr, Ar, Rr, f.irh2, so + next_o * PL, F, ov0, ov1, op);
         op_plane = next_o;
       }
       __syncthreads();  // every read of the slot refilled below is done
@@ -642,26 +571,6 @@ __global__ void __launch_bounds__(zm_threads<TY>(), TY <= 8 ? 2 : 1)
 }
 
 // ---- host side ----------------------------------------------------------------
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-    else
-      cudaGetLastError();
-  }
-  return fn;
-}
-
 template <int TY>
 cudaError_t zm_map(const Geom& g, const float* u, unsigned char* out) {
   static_assert(sizeof(CUtensorMap) <= ZM_MAP_BYTES, "tensor map storage");
@@ -689,26 +598,6 @@ void* zm_kernel(int mode, bool forced) {
   return forced ? (void*)step3d_o4_zm<TY, STEP_LAST, true> : (void*)step3d_o4_zm<TY, STEP_LAST, false>;
 }
 
-// Tile heights of the plan's kernel shapes: k = 0 (16 rows, one CTA per SM),
-// k = 1 (8 rows, two CTAs per SM).
-constexpr int ZM_TYS[ZM_SHAPES] = {16, 8};
-
-// Tile origin shift along one axis.  A tile's stress halo reaches 2 nodes and
-// its u tile 4 nodes beyond it, which covers every difference except where a
-// tile ends within 5 nodes of the high side: a stress node on SBP row n - 4
-// at the halo's last position reads u 3 further, and an own node on row n - 4
-// or n - 1 reads stresses 3 away.  That happens exactly when the last tile
-// holds 2 or 4 unknowns (Dirichlet high side) or 1, 3 or 5 (traction-free).
-// Starting the tiles `sh` nodes before the first unknown changes the last
-// tile's count; sh is the least multiple of `step` that avoids those counts.
-int zm_shift(int nu, int tile, bool hi_free, int step) {
-  for (int sh = 0; sh < tile; sh += step) {
-    const int last = (nu + sh) % tile == 0 ? tile : (nu + sh) % tile;
-    const bool bad = hi_free ? (last == 1 || last == 3 || last == 5) : (last == 2 || last == 4);
-    if (!bad) return sh;
-  }
-  return -1;
-}
 
 template <int TY>
 void plan_one(const Geom& g, const float* u_a, const float* u_b, int sms, int smem_max, ZmPlan& p, int k) {
@@ -799,29 +688,7 @@ cudaError_t launch_zmarch(const Geom& g, const ZmPlan& p, int k, const WaveField
   sc.bt12 = (float)(12.0 * 48.0 / 17.0);
   sc.shx = p.shx[k];
   sc.shy = p.shy[k];
-  // four taps per class: the nonzero columns of each closure row (mirrored and
-  // negated from the high side), the interior row, zero-weight padding
-  static const int kCols[4][4] = {{0, 1, 2, 3}, {0, 2, -1, -1}, {0, 1, 3, 4}, {0, 2, 4, 5}};
-  for (int c = 0; c < ZM_CLASSES; ++c)
-    for (int q = 0; q < 4; ++q) {
-      int off = 0;
-      double w = 0.0;
-      if (c == 4) {
-        static const int io[4] = {-2, -1, 1, 2};
-        static const double iw[4] = {1.0, -8.0, 8.0, -1.0};
-        off = io[q];
-        w = iw[q];
-      } else {
-        const int r = c < 4 ? c : c - 5;
-        const int j = kCols[r][q];
-        if (j >= 0) {
-          off = c < 4 ? j - r : r - j;
-          w = (c < 4 ? 12.0 : -12.0) * SBP_CLOSURE[r][j];
-        }
-      }
-      sc.toff[4 * c + q] = off;
-      sc.tcf[4 * c + q] = (float)w;
-    }
+  zm_class_taps(sc.toff, sc.tcf);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(p.grid[k]);
   cfg.blockDim = dim3(k == 0 ? ZmLayout<16>::NT : ZmLayout<8>::NT);
