@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libewh.so")
-SOURCES = ["ewh_stencil.cu", "ewh_zmarch.cu", "ewh_krylov.cu", "ewh_api.cu", "ewh_net.cu", "ewh_peak.cu"]
+SOURCES = ["ewh_stencil.cu", "ewh_zmarch.cu", "ewh_ymarch.cu", "ewh_krylov.cu", "ewh_api.cu", "ewh_net.cu", "ewh_peak.cu"]
 HEADERS = [os.path.join(CSRC, "ewh_internal.cuh"), os.path.join(CSRC, "ewh_march.cuh"), os.path.join(ROOT, "include", "ewh.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

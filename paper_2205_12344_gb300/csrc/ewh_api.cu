@@ -42,7 +42,7 @@ struct Wave {
   long long graph_Pi0_kernels = 0;
   int variant = -1;           // step-kernel variant (autotuner), -1 = not chosen yet
   int fallback = 0;           // fastest variant that is not the resident solve
-  float variant_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // per time level
+  float variant_ms[YM_VARIANT + 1] = {};  // per time level
   bool ready = false;
   // on-chip resident solve (2D order 4 FP32, one rhs): per-level scalars,
   // barrier words and the partition per CTA shape
@@ -50,14 +50,16 @@ struct Wave {
   double* d_wnew = nullptr;
   unsigned* bar = nullptr;
   ResidentPlan rplan[RS_SHAPES];
-  // fused 3D order-4 FP32 step: bulk-tensor maps of u_a / u_b, grid (control
-  // words in bar)
+  // fused marching FP32 order-4 step (3D z-march, 2D y-march): bulk-tensor
+  // maps of u_a / u_b, grid (control words in bar)
   ZmPlan zm;
 };
 
 // step-kernel variants of the 2D order-4 FP32 solve beyond the launcher's
 // own (split tiles 0..3, fused 4): 5 + shape = resident solve of that shape
 constexpr int VARIANT_RESIDENT = 5;
+static_assert(VARIANT_RESIDENT + RS_SHAPES == YM_VARIANT, "2D order-4 variants: split 0..3, fused 4, resident, y-march");
+inline bool is_resident_variant(int v) { return v >= VARIANT_RESIDENT && v < VARIANT_RESIDENT + RS_SHAPES; }
 
 }  // namespace
 
@@ -218,12 +220,15 @@ ewh_status build_wave(ewh_ctx* ctx, Wave<T>& w, const double* d_rho, const doubl
     EWH_CU(cudaMemcpy(w.d_wnew, hw.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
     for (int k = 0; k < RS_SHAPES; ++k) w.rplan[k] = plan_resident_o4(g, k);
   }
-  if (sizeof(T) == 4 && g.dim == 3 && ctx->order == 4 && !g.mapped) {
-    EWH_CU(alloc_zero(&w.bar, RS_BAR_WORDS, ctx->st));
-    const unsigned long long wait_ns = RS_WAIT_NS_DEFAULT;
-    EWH_CU(cudaStreamSynchronize(ctx->st));
-    EWH_CU(cudaMemcpy(w.bar + 2, &wait_ns, sizeof(wait_ns), cudaMemcpyHostToDevice));
-    w.zm = plan_zmarch(g, (const float*)w.u_a, (const float*)w.u_b, w.bar);
+  if (sizeof(T) == 4 && ctx->order == 4 && !g.mapped) {  // marching steps: 3D z-march, 2D y-march
+    if (!w.bar) {
+      EWH_CU(alloc_zero(&w.bar, RS_BAR_WORDS, ctx->st));
+      const unsigned long long wait_ns = RS_WAIT_NS_DEFAULT;
+      EWH_CU(cudaStreamSynchronize(ctx->st));
+      EWH_CU(cudaMemcpy(w.bar + 2, &wait_ns, sizeof(wait_ns), cudaMemcpyHostToDevice));
+    }
+    w.zm = g.dim == 3 ? plan_zmarch(g, (const float*)w.u_a, (const float*)w.u_b, w.bar)
+                      : plan_ymarch(g, (const float*)w.u_a, (const float*)w.u_b, w.bar);
   }
   return EWH_OK;
 }
@@ -326,7 +331,7 @@ std::string tune_key(const ewh_ctx* ctx) {
   for (auto& ch : name)
     if (ch == '"' || ch == ' ') ch = '_';
   const Geom& g = ctx->g;
-  return name + "|v3" + (ctx->allow_resident ? "" : "b") + (g.mapped ? "|map" : "") + "|d" + std::to_string(g.dim) +
+  return name + "|v4" + (ctx->allow_resident ? "" : "b") + (g.mapped ? "|map" : "") + "|d" + std::to_string(g.dim) +
          "|o" + std::to_string(ctx->order) + "|" +
          (sizeof(T) == 8 ? "f64" : "f32") + "|" + std::to_string(g.n[0]) + "x" + std::to_string(g.n[1]) + "x" +
          std::to_string(g.n[2]) + "|r" + std::to_string(g.nrhs);
@@ -336,8 +341,7 @@ std::string tune_key(const ewh_ctx* ctx) {
 // a partition that fits on chip, not a batch member, EWH_RESIDENT != 0.)
 template <typename T>
 bool resident_ok(const ewh_ctx* ctx, const Wave<T>& w, int v) {
-  if (sizeof(T) != 4 || v < VARIANT_RESIDENT || v >= VARIANT_RESIDENT + RS_SHAPES || !ctx->allow_resident)
-    return false;
+  if (sizeof(T) != 4 || !is_resident_variant(v) || !ctx->allow_resident) return false;
   const char* e = getenv("EWH_RESIDENT");
   if (e && e[0] == '0') return false;
   return w.rplan[v - VARIANT_RESIDENT].ok != 0;
@@ -373,14 +377,22 @@ cudaError_t enqueue_resident(ewh_ctx* ctx, Wave<T>& w, int v, bool forced, int n
   }
 }
 
+// The 2D order-4 FP32 y-march usable by this context?
+template <typename T>
+bool ymarch_ok(const ewh_ctx* ctx, const Wave<T>& w) {
+  return sizeof(T) == 4 && ctx->g.dim == 2 && ctx->order == 4 && !ctx->g.mapped && w.zm.ok[0] != 0;
+}
+
 template <typename T>
 void autotune(ewh_ctx* ctx, Wave<T>& w) {
   const int nbase = ctx->g.mapped ? 3 : step_variant_count(ctx->g.dim, ctx->order);
   const char* force = getenv("EWH_STEP2D_O4");
-  const bool forced_launcher = force && (force[0] == 's' || force[0] == 'f');
+  const bool forced_launcher = force && (force[0] == 's' || force[0] == 'f' || force[0] == 'y');
   bool any_res = false;
   for (int k = 0; k < RS_SHAPES && !forced_launcher; ++k) any_res |= resident_ok<T>(ctx, w, VARIANT_RESIDENT + k);
-  const int nv = any_res ? VARIANT_RESIDENT + RS_SHAPES : nbase;
+  const bool ym = ymarch_ok<T>(ctx, w);
+  // candidates: the launcher's own variants [0, nbase), the resident shapes, the y-march
+  const int nv = ym ? YM_VARIANT + 1 : (any_res ? VARIANT_RESIDENT + RS_SHAPES : nbase);
   w.fallback = 0;
   if (force && force[0] == 'r') {  // EWH_STEP2D_O4=r, r0, r1, r2: resident solve of that CTA shape
     const int k = (force[1] >= '0' && force[1] < '0' + RS_SHAPES) ? force[1] - '0' : 0;
@@ -388,6 +400,10 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
       w.variant = VARIANT_RESIDENT + k;
       return;
     }
+  }
+  if (force && strcmp(force, "ym") == 0 && ym) {  // EWH_STEP2D_O4=ym: the y-march
+    w.variant = YM_VARIANT;
+    return;
   }
   const char* off = getenv("EWH_AUTOTUNE");
   if (nv <= 1 || (off && off[0] == '0')) {
@@ -399,7 +415,7 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
   auto cache = read_tune_cache(path);
   for (auto& kv : cache)
     if (kv.first == key && kv.second >= 0 && kv.second < nv &&
-        (kv.second < VARIANT_RESIDENT || resident_ok<T>(ctx, w, kv.second))) {
+        (kv.second < nbase || resident_ok<T>(ctx, w, kv.second) || (kv.second == YM_VARIANT && ym))) {
       w.variant = kv.second;
       return;
     }
@@ -427,7 +443,7 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
   const int N = ctx->nt * ctx->periods;
   for (int v = 0; v < nv; ++v) {
     float per_level = 1e30f;
-    if (v >= VARIANT_RESIDENT) {
+    if (is_resident_variant(v)) {
       if (resident_ok<T>(ctx, w, v)) {
         const int ns = std::min(N, 40);
         bool ok = enqueue_resident<T>(ctx, w, v, false, std::min(N, 8)) == cudaSuccess;  // warm-up
@@ -439,7 +455,7 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
           per_level = ms / ns;
         cudaGetLastError();
       }
-    } else if (v < nbase) {
+    } else if (v < nbase || (v == YM_VARIANT && ym)) {
       Geom g = ctx->g;
       g.variant = v;
       bool ok = true;
@@ -458,7 +474,7 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
         best_base = v;
       }
     }
-    if (v < 8) w.variant_ms[v] = per_level;
+    if (v <= YM_VARIANT) w.variant_ms[v] = per_level;
     if (per_level < best_ms) {
       best_ms = per_level;
       best = v;
@@ -476,7 +492,7 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
   w.fallback = best_base;
   if (getenv("EWH_VERBOSE")) {
     fprintf(stderr, "ewh: autotune %s:", key.c_str());
-    for (int v = 0; v < nv && v < 8; ++v) fprintf(stderr, " v%d=%.4g", v, w.variant_ms[v]);
+    for (int v = 0; v < nv && v <= YM_VARIANT; ++v) fprintf(stderr, " v%d=%.4g", v, w.variant_ms[v]);
     fprintf(stderr, " ms/level -> %d\n", best);
   }
   cache.emplace_back(key, best);
@@ -487,7 +503,7 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
 template <typename T>
 cudaError_t enqueue_steps(ewh_ctx* ctx, Wave<T>& w, bool forced, long long* nl) {
   const int N = ctx->nt * ctx->periods;
-  if (w.variant >= VARIANT_RESIDENT) {  // all levels in one cooperative launch
+  if (is_resident_variant(w.variant)) {  // all levels in one cooperative launch
     cudaError_t e = enqueue_resident<T>(ctx, w, w.variant, forced, N);
     if (e == cudaSuccess && nl) *nl += 1;
     return e;
@@ -544,7 +560,7 @@ ewh_status ensure_graph(ewh_ctx* ctx, bool forced) {
     }
     ge = nullptr;
     cudaGetLastError();
-    if (attempt == 0 && w.variant >= VARIANT_RESIDENT) {  // not capturable here: per-level launches
+    if (attempt == 0 && is_resident_variant(w.variant)) {  // not capturable here: per-level launches
       w.variant = w.fallback;
       continue;
     }
@@ -1337,7 +1353,7 @@ ewh_status validate_desc(const ewh_grid_desc* d, int nrhs) {
   {  // one padded component must index in 32 bits (the step kernels use int offsets)
     long long cells = 1;
     for (int a = 0; a < d->dim; ++a)
-      cells *= ((d->n[a] + TILE_ROUND - 1) / TILE_ROUND) * TILE_ROUND + ((d->dim == 3 && a == 0) ? PAD3X : 2 * PAD);
+      cells *= ((d->n[a] + TILE_ROUND - 1) / TILE_ROUND) * TILE_ROUND + (a == 0 ? PAD3X : 2 * PAD);
     if (cells >= (1LL << 31)) return fail(nullptr, EWH_EINVAL, "grid too large: a padded component must hold < 2^31 nodes");
   }
   for (int k = 0; k < 2 * d->dim; ++k)
@@ -1644,7 +1660,7 @@ ewh_status create_impl(const ewh_grid_desc* desc, const double* xmap, const doub
   for (int a = 0; a < 3; ++a) {
     if (a < dim) {
       const int rounded = ((g.n[a] + TILE_ROUND - 1) / TILE_ROUND) * TILE_ROUND;
-      g.np[a] = rounded + ((dim == 3 && a == 0) ? PAD3X : 2 * PAD);
+      g.np[a] = rounded + (a == 0 ? PAD3X : 2 * PAD);
       g.off[a] = g.lo_free[a] ? 0 : 1;
       g.nu[a] = g.n[a] - (g.lo_free[a] ? 0 : 1) - (g.hi_free[a] ? 0 : 1);
     } else {
@@ -1654,7 +1670,7 @@ ewh_status create_impl(const ewh_grid_desc* desc, const double* xmap, const doub
     }
   }
   g.pz = dim == 3 ? PAD : 0;
-  g.padx = dim == 3 ? 8 - g.off[0] : PAD;
+  g.padx = 8 - g.off[0];
   g.plane = (long long)g.np[0] * g.np[1];
   g.field = g.plane * g.np[2];
   g.nodes = (long long)g.nu[0] * g.nu[1] * g.nu[2];
@@ -1871,7 +1887,7 @@ ewh_status ewh_get_info(const ewh_ctx* ctx, ewh_problem_info* info) {
   info->kernel_variant[1] = ctx->w32.variant;
   for (int k = 0; k < 8; ++k) info->resident[k] = -1;
   const int v = ctx->w32.variant;
-  if (v >= VARIANT_RESIDENT && v < VARIANT_RESIDENT + RS_SHAPES) {
+  if (is_resident_variant(v)) {
     const ResidentPlan& p = ctx->w32.rplan[v - VARIANT_RESIDENT];
     const int r[8] = {p.shape, p.px, p.py, p.bx, p.ex, p.by, RS_SHAPE_THREADS[p.shape], RS_SHAPE_PAIRS[p.shape]};
     for (int k = 0; k < 8; ++k) info->resident[k] = r[k];

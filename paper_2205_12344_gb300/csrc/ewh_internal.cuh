@@ -10,8 +10,8 @@ namespace ewh {
 // Padding (ghost layers, always zero) around the full node grid of every
 // device field.  Order 4 reads up to 6 nodes beyond a tile; tiles are at most
 // 32 wide and the padded extents are rounded up to a multiple of 32 first.
-// 3D fields pad x by 7 or 8 before and at least 8 after the grid (see
-// Geom::padx), with np[0] = rounded + PAD3X.
+// Along x the fields pad 7 or 8 nodes before and at least 8 after the grid
+// (see Geom::padx), with np[0] = rounded + PAD3X.
 constexpr int PAD = 6;
 constexpr int TILE_ROUND = 32;
 constexpr int PAD3X = 16;
@@ -23,9 +23,9 @@ struct Geom {
   int lo_free[3];  // 1 if the low side of the axis is a free surface
   int hi_free[3];
   int np[3];       // padded extents (np[2] = 1 in 2D)
-  int padx;        // padding before x = 0 (2D: PAD; 3D: 8 - off[0], so the first unknown node of
-                   // every row sits at a padded x that is a multiple of 4: 16-byte aligned rows of
-                   // unknown pairs for vector and bulk-tensor access)
+  int padx;        // padding before x = 0: 8 - off[0], so the first unknown node of every row
+                   // sits at a padded x that is a multiple of 4 (16-byte aligned rows of unknown
+                   // pairs for vector and bulk-tensor access)
   int pz;          // padding along z (PAD in 3D, 0 in 2D)
   long long plane; // np[0] * np[1]
   long long field; // elements of one padded component: plane * np[2]
@@ -83,11 +83,12 @@ struct StepScalars {
 
 enum StepMode { STEP_FIRST = 0, STEP_MID = 1, STEP_LAST = 2 };
 
-// Plan of the fused 3D order-4 FP32 z-march step (ewh_zmarch.cu): bulk-tensor
-// maps of both u buffers, the persistent grid and the control words (wait
-// limit in ns at [2..3] as a u64, give-up count at [4]).
-// Shapes: k = 0 tiles of 32 x 16 nodes (one CTA per SM), k = 1 tiles of
-// 32 x 8 (two CTAs per SM).
+// Plan of the fused marching FP32 order-4 steps: bulk-tensor maps of both u
+// buffers, the persistent grid and the control words (wait limit in ns at
+// [2..3] as a u64, give-up count at [4]).
+// 3D z-march (ewh_zmarch.cu), shapes k = 0 tiles of 32 x 16 nodes (one CTA
+// per SM), k = 1 tiles of 32 x 8 (two CTAs per SM); 2D y-march
+// (ewh_ymarch.cu), slot 0: strips of 60 columns, one warp per CTA.
 constexpr int ZM_MAP_BYTES = 128;
 constexpr int ZM_SHAPES = 2;
 struct ZmPlan {
@@ -218,6 +219,14 @@ cudaError_t launch_resident_o4(const Geom& g, const ResidentPlan& p, const Resid
 // ---- fused 3D order-4 FP32 step (ewh_zmarch.cu) ------------------------------
 ZmPlan plan_zmarch(const Geom& g, const float* u_a, const float* u_b, unsigned* ctl);
 cudaError_t launch_zmarch(const Geom& g, const ZmPlan& p, int shape, const WaveFields<float>& f, StepMode mode,
+                          const StepScalars& s, cudaStream_t st);
+
+// ---- fused 2D order-4 FP32 step (ewh_ymarch.cu) ------------------------------
+// Step-kernel variant of the 2D order-4 FP32 launcher that runs it (after
+// the split tiles 0..3, the fused kernel 4 and the resident shapes 5..7).
+constexpr int YM_VARIANT = 8;
+ZmPlan plan_ymarch(const Geom& g, const float* u_a, const float* u_b, unsigned* ctl);
+cudaError_t launch_ymarch(const Geom& g, const ZmPlan& p, const WaveFields<float>& f, StepMode mode,
                           const StepScalars& s, cudaStream_t st);
 
 // Message for ewh_last_error(NULL) of calls that have no context.

@@ -755,9 +755,9 @@ static cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cud
 
 // 2D order-4 kernel variants (Geom::variant, chosen per context by the
 // autotuner): 0..3 = stress + divergence launches with 32x8, 32x16, 64x8 or
-// 64x4 blocks, 4 = single fused launch.  EWH_STEP2D_O4=fused|split overrides
-// it (read whenever launches are enqueued; a context captures its step graph
-// once, on first use).
+// 64x4 blocks, 4 = single fused launch, YM_VARIANT = the FP32 y-march
+// (ewh_ymarch.cu).  EWH_STEP2D_O4=fused|split|ym overrides it (read whenever
+// launches are enqueued; a context captures its step graph once, on first use).
 // Mapped 2D grids: 0 = fused curv_step2d with 32x8 outputs per block, 1 =
 // curv_stress2d + curv_div2d, 2 = fused with 32x16 outputs (FP32; FP64 runs 32x8).  Geom::variant
 // from the autotuner; EWH_CURV=fused|fused16|split overrides it.
@@ -1147,6 +1147,17 @@ static cudaError_t launch_mode(const Geom& g, int order, const WaveFields<T>& f,
     if (e != cudaSuccess) return e;
     if (nl) *nl += 2;
     return cudaGetLastError();
+  }
+  if constexpr (sizeof(T) == 4 && MODE != 3) {
+    // fused y-march: autotuner variant YM_VARIANT; EWH_STEP2D_O4=ym forces it
+    const char* ev = getenv("EWH_STEP2D_O4");
+    const bool ym = ev ? strcmp(ev, "ym") == 0 : g.variant == YM_VARIANT;
+    if (g.dim == 2 && ym && f.zm && f.zm->ok[0]) {
+      cudaError_t e = launch_ymarch(g, *f.zm, f, (StepMode)MODE, s, st);
+      if (e != cudaSuccess) return e;
+      if (nl) *nl += 1;
+      return cudaGetLastError();
+    }
   }
   if (g.dim == 2 && step2d_o4_variant(g) == 1) {
     constexpr int TY = o4_tile_y<T>();
