@@ -109,13 +109,15 @@ typedef struct {
   int kernel_variant[2]; /* step-kernel variant picked by the autotuner for the
                             FP64 / FP32 wave solves (-1 = not picked yet; it is
                             picked on the first solve of that precision) */
-  int resident[8];     /* when the FP32 wave solve runs on chip in one cooperative
-                          launch (2D, order 4, one rhs): its partition -- CTA
-                          shape index, CTAs along x and y, interior block width,
-                          first block width, block height (nodes), threads per
-                          CTA, register node pairs per thread; CTA (cx, cy)
-                          owns x from X0 = cx ? first + (cx-1) width : 0 and
-                          y from cy height.  All -1 otherwise. */
+  int resident[10];    /* when the FP32 wave solve runs on chip (2D, order 4),
+                          one cooperative launch per group of right-hand sides:
+                          its partition -- CTA shape index, CTAs along x and y
+                          per rhs, interior block width, first block width,
+                          block height (nodes), threads per CTA, register node
+                          pairs per thread, rhs per launch, launches; CTA
+                          (cx, cy) of a rhs owns x from X0 = cx ? first +
+                          (cx-1) width : 0 and y from cy height.  All -1
+                          otherwise. */
 } ewh_problem_info;
 
 typedef struct {

@@ -26,7 +26,7 @@ class ewh_problem_info(ctypes.Structure):
     _fields_ = [("nt", ctypes.c_int), ("periods", ctypes.c_int), ("dt", ctypes.c_double),
                 ("omega", ctypes.c_double), ("omega_tilde", ctypes.c_double), ("kt", ctypes.c_double),
                 ("nodes", ctypes.c_longlong), ("n_unknowns", ctypes.c_longlong), ("nrhs", ctypes.c_int),
-                ("nu", ctypes.c_int * 3), ("kernel_variant", ctypes.c_int * 2), ("resident", ctypes.c_int * 8)]
+                ("nu", ctypes.c_int * 3), ("kernel_variant", ctypes.c_int * 2), ("resident", ctypes.c_int * 10)]
 
 
 class ewh_solve_info(ctypes.Structure):

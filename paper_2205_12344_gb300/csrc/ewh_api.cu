@@ -53,11 +53,18 @@ struct Wave {
   // fused marching FP32 order-4 step (3D z-march, 2D y-march): bulk-tensor
   // maps of u_a / u_b, grid (control words in bar)
   ZmPlan zm;
+  // CG iterations under device control (a while-conditional graph): 0 not
+  // built yet, 1 built, -1 unavailable (the host drives every iteration)
+  cudaGraphExec_t cg_loop = nullptr;
+  int cg_loop_state = 0;
+  long long cg_loop_kernels = 0;  // kernels of one pass
 };
 
 // step-kernel variants of the 2D order-4 FP32 solve beyond the launcher's
 // own (split tiles 0..3, fused 4): 5 + shape = resident solve of that shape
 constexpr int VARIANT_RESIDENT = 5;
+// longest window of CG iterations under device control between host polls
+constexpr int CG_WINDOW_MAX = 256;
 static_assert(VARIANT_RESIDENT + RS_SHAPES == YM_VARIANT, "2D order-4 variants: split 0..3, fused 4, resident, y-march");
 inline bool is_resident_variant(int v) { return v >= VARIANT_RESIDENT && v < VARIANT_RESIDENT + RS_SHAPES; }
 
@@ -90,9 +97,17 @@ struct ewh_ctx {
   double* h_scal = nullptr; // pinned host mirror of scal
   int* h_act = nullptr;     // pinned host mirror of active (nrhs)
   int* h_flag = nullptr;    // pinned host mirror of flags
+  // device-side CG loop control: per-rhs replacement anchors then tol and
+  // drop (nrhs + 2), [0] iterations of the current window, [1] window length,
+  // the window's history; pinned mirrors
+  double* d_anchor = nullptr;
+  int* d_loop = nullptr;
+  double* d_hist = nullptr;
+  double* h_anchor = nullptr;
+  int* h_loop = nullptr;
+  double* h_hist = nullptr;
   int nblk = 1;
   long long launches = 0;
-  bool allow_resident = true;  // false for batch members (their branches run concurrently)
   // implicit scheme (Section 4.4; FP64, dense unknown layout): level vectors,
   // inner-solve vectors, f/rho, device scalars of the inner CG
   int implicit = 0;
@@ -203,7 +218,7 @@ ewh_status build_wave(ewh_ctx* ctx, Wave<T>& w, const double* d_rho, const doubl
       }
   }
   EWH_CU(cudaGetLastError());
-  if (sizeof(T) == 4 && g.dim == 2 && ctx->order == 4 && g.nrhs == 1 && !g.mapped) {
+  if (sizeof(T) == 4 && g.dim == 2 && ctx->order == 4 && !g.mapped) {
     const int N = ctx->nt * ctx->periods;
     std::vector<double> hc(N), hw(N);
     for (int n = 0; n < N; ++n) {  // the same values as the per-level launches get
@@ -235,6 +250,7 @@ ewh_status build_wave(ewh_ctx* ctx, Wave<T>& w, const double* d_rho, const doubl
 
 template <typename T>
 void free_wave(Wave<T>& w) {
+  if (w.cg_loop) cudaGraphExecDestroy(w.cg_loop);
   if (w.graph_S) cudaGraphExecDestroy(w.graph_S);
   if (w.graph_Pi0) cudaGraphExecDestroy(w.graph_Pi0);
   cudaFree(w.u_a);
@@ -331,17 +347,17 @@ std::string tune_key(const ewh_ctx* ctx) {
   for (auto& ch : name)
     if (ch == '"' || ch == ' ') ch = '_';
   const Geom& g = ctx->g;
-  return name + "|v4" + (ctx->allow_resident ? "" : "b") + (g.mapped ? "|map" : "") + "|d" + std::to_string(g.dim) +
+  return name + "|v4" + (g.mapped ? "|map" : "") + "|d" + std::to_string(g.dim) +
          "|o" + std::to_string(ctx->order) + "|" +
          (sizeof(T) == 8 ? "f64" : "f32") + "|" + std::to_string(g.n[0]) + "x" + std::to_string(g.n[1]) + "x" +
          std::to_string(g.n[2]) + "|r" + std::to_string(g.nrhs);
 }
 
-// Resident variant v usable by this context?  (FP32 2D order 4, one rhs,
-// a partition that fits on chip, not a batch member, EWH_RESIDENT != 0.)
+// Resident variant v usable by this context?  (FP32 2D order 4, a
+// partition that fits on chip, EWH_RESIDENT != 0.)
 template <typename T>
 bool resident_ok(const ewh_ctx* ctx, const Wave<T>& w, int v) {
-  if (sizeof(T) != 4 || !is_resident_variant(v) || !ctx->allow_resident) return false;
+  if (sizeof(T) != 4 || !is_resident_variant(v)) return false;
   const char* e = getenv("EWH_RESIDENT");
   if (e && e[0] == '0') return false;
   return w.rplan[v - VARIANT_RESIDENT].ok != 0;
@@ -390,8 +406,9 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
   const bool forced_launcher = force && (force[0] == 's' || force[0] == 'f' || force[0] == 'y');
   bool any_res = false;
   for (int k = 0; k < RS_SHAPES && !forced_launcher; ++k) any_res |= resident_ok<T>(ctx, w, VARIANT_RESIDENT + k);
-  const bool ym = ymarch_ok<T>(ctx, w);
-  // candidates: the launcher's own variants [0, nbase), the resident shapes, the y-march
+  const bool ym = ymarch_ok<T>(ctx, w) && !forced_launcher;
+  // candidates: the launcher's own variants [0, nbase), the resident shapes,
+  // the y-march (only the launcher's own when the environment names one)
   const int nv = ym ? YM_VARIANT + 1 : (any_res ? VARIANT_RESIDENT + RS_SHAPES : nbase);
   w.fallback = 0;
   if (force && force[0] == 'r') {  // EWH_STEP2D_O4=r, r0, r1, r2: resident solve of that CTA shape
@@ -401,7 +418,7 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
       return;
     }
   }
-  if (force && strcmp(force, "ym") == 0 && ym) {  // EWH_STEP2D_O4=ym: the y-march
+  if (force && strcmp(force, "ym") == 0 && ymarch_ok<T>(ctx, w)) {  // EWH_STEP2D_O4=ym: the y-march
     w.variant = YM_VARIANT;
     return;
   }
@@ -410,12 +427,13 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
     w.variant = 0;
     return;
   }
-  const std::string path = tune_cache_path();
+  // a choice made under EWH_STEP2D_O4 (a restricted candidate set) is not cached
+  const std::string path = forced_launcher ? std::string() : tune_cache_path();
   const std::string key = tune_key<T>(ctx);
   auto cache = read_tune_cache(path);
   for (auto& kv : cache)
     if (kv.first == key && kv.second >= 0 && kv.second < nv &&
-        (kv.second < nbase || resident_ok<T>(ctx, w, kv.second) || (kv.second == YM_VARIANT && ym))) {
+        (kv.second < nbase || (any_res && resident_ok<T>(ctx, w, kv.second)) || (kv.second == YM_VARIANT && ym))) {
       w.variant = kv.second;
       return;
     }
@@ -444,7 +462,7 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
   for (int v = 0; v < nv; ++v) {
     float per_level = 1e30f;
     if (is_resident_variant(v)) {
-      if (resident_ok<T>(ctx, w, v)) {
+      if (any_res && resident_ok<T>(ctx, w, v)) {  // not when the environment names a per-level launcher
         const int ns = std::min(N, 40);
         bool ok = enqueue_resident<T>(ctx, w, v, false, std::min(N, 8)) == cudaSuccess;  // warm-up
         cudaEventRecord(e0, ctx->st);
@@ -503,9 +521,9 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
 template <typename T>
 cudaError_t enqueue_steps(ewh_ctx* ctx, Wave<T>& w, bool forced, long long* nl) {
   const int N = ctx->nt * ctx->periods;
-  if (is_resident_variant(w.variant)) {  // all levels in one cooperative launch
+  if (is_resident_variant(w.variant)) {  // all levels in one cooperative launch per group of rhs
     cudaError_t e = enqueue_resident<T>(ctx, w, w.variant, forced, N);
-    if (e == cudaSuccess && nl) *nl += 1;
+    if (e == cudaSuccess && nl) *nl += w.rplan[w.variant - VARIANT_RESIDENT].groups;
     return e;
   }
   Geom gv = ctx->g;
@@ -892,12 +910,21 @@ ewh_status cg_begin(ewh_ctx* ctx, double* r, double tol, double drop, CgState& c
   return EWH_OK;
 }
 
-// One CG iteration on ctx->st, ending with the copies of the scalars, the
-// active mask and the flags into pinned host memory.  With direct_steps the
-// leapfrog launches are enqueued one by one (inside a batch capture);
-// otherwise the context's captured S graph is launched.
+// Scalars, active mask and flags of the last iteration into pinned host memory.
+cudaError_t copy_cg_scalars(ewh_ctx* ctx) {
+  const int R = ctx->g.nrhs;
+  cudaError_t e = cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * S_N * R, cudaMemcpyDeviceToHost, ctx->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_act, ctx->active, sizeof(int) * R, cudaMemcpyDeviceToHost, ctx->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_flag, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->st);
+  return e;
+}
+
+// One CG iteration on ctx->st, ending (with `copies`) with the copies of the
+// scalars, the active mask and the flags into pinned host memory.  With
+// direct_steps the leapfrog launches are enqueued one by one (inside a batch
+// or loop capture); otherwise the context's captured S graph is launched.
 template <typename T>
-ewh_status cg_enqueue_iteration(ewh_ctx* ctx, double* x, double* r, bool direct_steps) {
+ewh_status cg_enqueue_iteration(ewh_ctx* ctx, double* x, double* r, bool direct_steps, bool copies = true) {
   const Geom& g = ctx->g;
   const int R = g.nrhs;
   Wave<T>& w = wave_of<T>(ctx);
@@ -924,9 +951,7 @@ ewh_status cg_enqueue_iteration(ewh_ctx* ctx, double* x, double* r, bool direct_
   EWH_CU(launch_cg_beta(R, ctx->part, ctx->nblk, sc(ctx, S_RR), sc(ctx, S_BB), sc(ctx, S_BETA), sc(ctx, S_RES),
                         ctx->active, ctx->st));
   ctx->launches += 5;
-  EWH_CU(cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * S_N * R, cudaMemcpyDeviceToHost, ctx->st));
-  EWH_CU(cudaMemcpyAsync(ctx->h_act, ctx->active, sizeof(int) * R, cudaMemcpyDeviceToHost, ctx->st));
-  EWH_CU(cudaMemcpyAsync(ctx->h_flag, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  if (copies) EWH_CU(copy_cg_scalars(ctx));
   return EWH_OK;
 }
 
@@ -979,16 +1004,114 @@ double cg_worst_true(const CgState& cs) {
   return m;
 }
 
+// Iterations per host poll of the device-controlled CG loop (EWH_CG_POLL,
+// default 32; 1 or less: the host drives every iteration).
+int cg_window() {
+  const char* e = getenv("EWH_CG_POLL");
+  const int m = e ? atoi(e) : 32;
+  return std::min(m, CG_WINDOW_MAX);
+}
+
+// Build the device-controlled CG loop of precision T on (ctx->kx, ctx->kr):
+// a graph whose while-conditional node runs one iteration per pass (the
+// leapfrog launches, the Krylov kernels, then cg_control, which sets the
+// condition), so a window of iterations runs without the host.  Any failure
+// (a launch the driver does not take inside a conditional body) leaves
+// cg_loop_state = -1 and the host-driven loop in charge.
+template <typename T>
+void ensure_cg_loop(ewh_ctx* ctx) {
+  Wave<T>& w = wave_of<T>(ctx);
+  if (w.cg_loop_state != 0 || ctx->implicit) {
+    if (ctx->implicit) w.cg_loop_state = -1;
+    return;
+  }
+  w.cg_loop_state = -1;
+  cudaGraph_t graph = nullptr;
+  cudaGraphConditionalHandle h;
+  if (cudaGraphCreate(&graph, 0) != cudaSuccess ||
+      cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return;
+  }
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  bool ok = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np) == cudaSuccess;
+  if (ok) {
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(ctx->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+         cudaSuccess;
+    if (ok) {
+      const long long l0 = ctx->launches;
+      ok = cg_enqueue_iteration<T>(ctx, ctx->kx, ctx->kr, true, false) == EWH_OK &&
+           launch_cg_control(h, ctx->g.nrhs, sc(ctx, S_RES), ctx->active, ctx->d_anchor, ctx->flags, ctx->d_loop,
+                             ctx->d_hist, ctx->st) == cudaSuccess;
+      w.cg_loop_kernels = ctx->launches - l0 + 1;
+      ctx->launches = l0;  // captured, not run
+      cudaGraph_t captured = nullptr;
+      ok = cudaStreamEndCapture(ctx->st, &captured) == cudaSuccess && ok;
+    }
+  }
+  ok = ok && cudaGraphInstantiate(&w.cg_loop, graph, 0) == cudaSuccess;
+  cudaGraphDestroy(graph);
+  if (!ok) {
+    if (w.cg_loop) cudaGraphExecDestroy(w.cg_loop);
+    w.cg_loop = nullptr;
+    cudaGetLastError();
+    if (getenv("EWH_VERBOSE")) fprintf(stderr, "ewh: device-controlled CG loop unavailable: host polls each iteration\n");
+    return;
+  }
+  w.cg_loop_state = 1;
+}
+
 template <typename T>
 ewh_status run_cg(ewh_ctx* ctx, double* x, double* r, double tol, int maxit, double drop, ewh_solve_info* inf,
                   double* rel_out) {
   CgState cs;
   ewh_status st = cg_begin<T>(ctx, r, tol, drop, cs);
   if (st != EWH_OK) return st;
+  const int R = ctx->g.nrhs;
+  const int m = cg_window();
+  Wave<T>& w = wave_of<T>(ctx);
+  // the loop graph works on x = kx, r = kr; tol and drop follow the anchors
+  if (m > 1 && x == ctx->kx && r == ctx->kr && w.cg_loop_state == 0) ensure_cg_loop<T>(ctx);
+  const bool dev = m > 1 && x == ctx->kx && r == ctx->kr && w.cg_loop_state == 1;
   while (cs.any_active && inf->iters < maxit) {
-    st = cg_enqueue_iteration<T>(ctx, x, r, false);
-    if (st != EWH_OK) return st;
-    EWH_CU(cudaStreamSynchronize(ctx->st));
+    if (dev) {
+      // a window of iterations under device control; the host then takes the
+      // decisions of the window's last iteration (as after any iteration)
+      const int limit = std::min(m, maxit - inf->iters);
+      for (int k = 0; k < R; ++k) ctx->h_anchor[k] = cs.anchor[k];
+      ctx->h_anchor[R] = tol;
+      ctx->h_anchor[R + 1] = drop;
+      ctx->h_loop[0] = 0;
+      ctx->h_loop[1] = limit;
+      EWH_CU(cudaMemcpyAsync(ctx->d_anchor, ctx->h_anchor, sizeof(double) * (R + 2), cudaMemcpyHostToDevice,
+                             ctx->st));
+      EWH_CU(cudaMemcpyAsync(ctx->d_loop, ctx->h_loop, sizeof(int) * 2, cudaMemcpyHostToDevice, ctx->st));
+      EWH_CU(cudaGraphLaunch(w.cg_loop, ctx->st));
+      EWH_CU(copy_cg_scalars(ctx));
+      EWH_CU(cudaMemcpyAsync(ctx->h_loop, ctx->d_loop, sizeof(int) * 2, cudaMemcpyDeviceToHost, ctx->st));
+      EWH_CU(cudaMemcpyAsync(ctx->h_hist, ctx->d_hist, sizeof(double) * limit, cudaMemcpyDeviceToHost, ctx->st));
+      EWH_CU(cudaStreamSynchronize(ctx->st));
+      const int it = ctx->h_loop[0];
+      if (it < 1 || it > limit) return fail(ctx, EWH_ECUDA, "device-controlled CG loop ran no iteration");
+      ctx->launches += (long long)it * w.cg_loop_kernels;
+      for (int i = 0; i + 1 < it; ++i) {  // iterations that needed no host decision
+        ctx->history.push_back(ctx->h_hist[i]);
+        ++inf->iters;
+        if (sizeof(T) == 8) ++inf->s_applies_fp64;
+        else ++inf->s_applies;
+      }
+    } else {
+      st = cg_enqueue_iteration<T>(ctx, x, r, false);
+      if (st != EWH_OK) return st;
+      EWH_CU(cudaStreamSynchronize(ctx->st));
+    }
     st = cg_after_iteration<T>(ctx, x, r, cs, inf);
     if (st != EWH_OK) {
       *rel_out = cg_worst_true(cs);
@@ -1383,6 +1506,11 @@ struct ewh_batch {
   std::vector<cudaEvent_t> joins;
   cudaGraphExec_t iter_graph = nullptr;
   std::vector<int> graph_members;
+  // CG windows under device control: one while-conditional node per member
+  cudaGraphExec_t loop_graph = nullptr;
+  std::vector<int> loop_members;
+  std::vector<long long> loop_kernels;  // per member: kernels of one pass
+  bool loop_failed = false;
   int precision = EWH_FP64;
   long long launches = 0;
   std::string err = "no error";
@@ -1396,20 +1524,29 @@ ewh_status bfail(ewh_batch* b, ewh_status s, const std::string& m) {
 }
 
 // Capture one graph whose branches enqueue `fn(k)` on member k's stream.
+// The branches run concurrently, except when a member runs the resident
+// solve: a cooperative launch must have its whole grid resident, so then the
+// members follow one another.
 template <typename F>
 ewh_status capture_branches(ewh_batch* b, const std::vector<int>& members, F fn, cudaGraphExec_t* out) {
+  bool serial = false;
+  if (b->precision != EWH_FP64)
+    for (int k : members) serial = serial || is_resident_variant(b->p[k]->w32.variant);
   cudaGraph_t graph = nullptr;
   if (cudaStreamBeginCapture(b->master, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return bfail(b, EWH_ECUDA, "batch capture could not start");
   cudaError_t e = cudaEventRecord(b->fork, b->master);
   ewh_status st = EWH_OK;
+  cudaEvent_t prev = b->fork;
   for (int k : members) {
     ewh_ctx* c = b->p[k];
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->st, b->fork, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->st, serial ? prev : b->fork, 0);
     if (e == cudaSuccess && st == EWH_OK) st = fn(k);
     if (e == cudaSuccess) e = cudaEventRecord(b->joins[k], c->st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->master, b->joins[k], 0);
+    if (e == cudaSuccess && !serial) e = cudaStreamWaitEvent(b->master, b->joins[k], 0);
+    prev = b->joins[k];
   }
+  if (e == cudaSuccess && serial) e = cudaStreamWaitEvent(b->master, prev, 0);
   const cudaError_t e2 = cudaStreamEndCapture(b->master, &graph);
   if (e != cudaSuccess || e2 != cudaSuccess || st != EWH_OK) {
     if (graph) cudaGraphDestroy(graph);
@@ -1421,6 +1558,77 @@ ewh_status capture_branches(ewh_batch* b, const std::vector<int>& members, F fn,
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return bfail(b, EWH_ECUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
   return EWH_OK;
+}
+
+// Order the members' own streams (residual replacements, mask uploads of the
+// host decisions) before the next batch graph launch on the master stream.
+bool members_before_master(ewh_batch* b, const std::vector<int>& members) {
+  for (int k : members)
+    if (cudaEventRecord(b->joins[k], b->p[k]->st) != cudaSuccess ||
+        cudaStreamWaitEvent(b->master, b->joins[k], 0) != cudaSuccess)
+      return false;
+  return true;
+}
+
+// The batch's device-controlled CG windows: per member a while-conditional
+// node whose body is one iteration of that member (its leapfrog launches, the
+// Krylov kernels, the control kernel); the members' nodes run concurrently,
+// or one after another when a member runs the resident solve.  Returns false
+// (and the host polls every iteration) when the driver does not take it.
+template <typename T>
+bool build_batch_loop(ewh_batch* b, const std::vector<int>& members) {
+  if (b->loop_graph) cudaGraphExecDestroy(b->loop_graph);
+  b->loop_graph = nullptr;
+  bool serial = false;
+  if (sizeof(T) == 4)
+    for (int k : members) serial = serial || is_resident_variant(b->p[k]->w32.variant);
+  cudaGraph_t graph = nullptr;
+  bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
+  b->loop_kernels.assign(b->p.size(), 0);
+  cudaGraphNode_t prev = nullptr;
+  for (int k : members) {
+    if (!ok) break;
+    ewh_ctx* ctx = b->p[k];
+    if (ctx->implicit) {
+      ok = false;
+      break;
+    }
+    cudaGraphConditionalHandle h;
+    ok = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    ok = ok && cudaGraphAddNode(&node, graph, (serial && prev) ? &prev : nullptr, nullptr, (serial && prev) ? 1 : 0,
+                                &np) == cudaSuccess;
+    if (!ok) break;
+    ok = cudaStreamBeginCaptureToGraph(ctx->st, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (!ok) break;
+    const long long l0 = ctx->launches;
+    ok = cg_enqueue_iteration<T>(ctx, ctx->kx, ctx->kr, true, false) == EWH_OK &&
+         launch_cg_control(h, ctx->g.nrhs, sc(ctx, S_RES), ctx->active, ctx->d_anchor, ctx->flags, ctx->d_loop,
+                           ctx->d_hist, ctx->st) == cudaSuccess;
+    b->loop_kernels[k] = ctx->launches - l0 + 1;
+    ctx->launches = l0;  // captured, not run
+    cudaGraph_t captured = nullptr;
+    ok = cudaStreamEndCapture(ctx->st, &captured) == cudaSuccess && ok;
+    prev = node;
+  }
+  ok = ok && cudaGraphInstantiate(&b->loop_graph, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) {
+    if (b->loop_graph) cudaGraphExecDestroy(b->loop_graph);
+    b->loop_graph = nullptr;
+    cudaGetLastError();
+    b->loop_failed = true;
+    if (getenv("EWH_VERBOSE")) fprintf(stderr, "ewh: device-controlled batch CG unavailable: host polls each iteration\n");
+    return false;
+  }
+  b->loop_members = members;
+  return true;
 }
 
 template <typename T>
@@ -1453,7 +1661,67 @@ ewh_status batch_solve_T(ewh_batch* b, double tol, int maxit, double* const* v_o
   std::vector<int> members;
   for (int k = 0; k < P; ++k)
     if (cs[k].any_active) members.push_back(k);
+  const int window = cg_window();
   while (!members.empty()) {
+    bool dev = window > 1 && !b->loop_failed;
+    if (dev && (members != b->loop_members || !b->loop_graph)) dev = build_batch_loop<T>(b, members);
+    if (dev) {
+      // a window of iterations of every member under device control; then, per
+      // member, the host decisions of its window's last iteration
+      for (int k : members) {
+        ewh_ctx* ctx = b->p[k];
+        const int R = ctx->g.nrhs;
+        for (int q = 0; q < R; ++q) ctx->h_anchor[q] = cs[k].anchor[q];
+        ctx->h_anchor[R] = tol;
+        ctx->h_anchor[R + 1] = drop;
+        ctx->h_loop[0] = 0;
+        ctx->h_loop[1] = std::max(1, std::min(window, maxit - inf[k].iters));
+        if (cudaMemcpyAsync(ctx->d_anchor, ctx->h_anchor, sizeof(double) * (R + 2), cudaMemcpyHostToDevice,
+                            b->master) != cudaSuccess ||
+            cudaMemcpyAsync(ctx->d_loop, ctx->h_loop, sizeof(int) * 2, cudaMemcpyHostToDevice, b->master) !=
+                cudaSuccess)
+          return bfail(b, EWH_ECUDA, "batch window setup failed");
+      }
+      bool ok = members_before_master(b, members) && cudaGraphLaunch(b->loop_graph, b->master) == cudaSuccess;
+      for (int k : members) {
+        ewh_ctx* ctx = b->p[k];
+        const int R = ctx->g.nrhs;
+        ok = ok &&
+             cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * S_N * R, cudaMemcpyDeviceToHost, b->master) ==
+                 cudaSuccess &&
+             cudaMemcpyAsync(ctx->h_act, ctx->active, sizeof(int) * R, cudaMemcpyDeviceToHost, b->master) ==
+                 cudaSuccess &&
+             cudaMemcpyAsync(ctx->h_flag, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost, b->master) == cudaSuccess &&
+             cudaMemcpyAsync(ctx->h_loop, ctx->d_loop, sizeof(int) * 2, cudaMemcpyDeviceToHost, b->master) ==
+                 cudaSuccess &&
+             cudaMemcpyAsync(ctx->h_hist, ctx->d_hist, sizeof(double) * window, cudaMemcpyDeviceToHost, b->master) ==
+                 cudaSuccess;
+      }
+      if (!ok || cudaStreamSynchronize(b->master) != cudaSuccess)
+        return bfail(b, EWH_ECUDA, std::string("batch window failed: ") + cudaGetErrorString(cudaGetLastError()));
+      std::vector<int> next;
+      for (int k : members) {
+        ewh_ctx* ctx = b->p[k];
+        const int it = ctx->h_loop[0];
+        if (it < 1) return bfail(b, EWH_ECUDA, "device-controlled batch window ran no iteration");
+        b->launches += (long long)it * b->loop_kernels[k];
+        for (int i = 0; i + 1 < it; ++i) {  // iterations that needed no host decision
+          ctx->history.push_back(ctx->h_hist[i]);
+          ++inf[k].iters;
+          if (sizeof(T) == 8) ++inf[k].s_applies_fp64;
+          else ++inf[k].s_applies;
+        }
+        ewh_status s = cg_after_iteration<T>(ctx, ctx->kx, ctx->kr, cs[k], &inf[k]);
+        if (s == EWH_EBREAKDOWN) {
+          fallback[k] = 1;
+          continue;
+        }
+        if (s != EWH_OK) return bfail(b, s, ctx->err);
+        if (cs[k].any_active && inf[k].iters < maxit) next.push_back(k);
+      }
+      members.swap(next);
+      continue;
+    }
     if (members != b->graph_members || !b->iter_graph) {
       if (b->iter_graph) cudaGraphExecDestroy(b->iter_graph);
       b->iter_graph = nullptr;
@@ -1463,7 +1731,8 @@ ewh_status batch_solve_T(ewh_batch* b, double tol, int maxit, double* const* v_o
       if (s != EWH_OK) return s;
       b->graph_members = members;
     }
-    if (cudaGraphLaunch(b->iter_graph, b->master) != cudaSuccess || cudaStreamSynchronize(b->master) != cudaSuccess)
+    if (!members_before_master(b, members) || cudaGraphLaunch(b->iter_graph, b->master) != cudaSuccess ||
+        cudaStreamSynchronize(b->master) != cudaSuccess)
       return bfail(b, EWH_ECUDA, std::string("batch iteration failed: ") + cudaGetErrorString(cudaGetLastError()));
     std::vector<int> next;
     for (int k : members) {
@@ -1763,7 +2032,13 @@ ewh_status create_impl(const ewh_grid_desc* desc, const double* xmap, const doub
          alloc_zero(&ctx->active, nrhs, ctx->st) == cudaSuccess && alloc_zero(&ctx->flags, 1, ctx->st) == cudaSuccess &&
          cudaMallocHost(&ctx->h_scal, sizeof(double) * S_N * nrhs) == cudaSuccess &&
          cudaMallocHost(&ctx->h_act, sizeof(int) * nrhs) == cudaSuccess &&
-         cudaMallocHost(&ctx->h_flag, sizeof(int)) == cudaSuccess;
+         cudaMallocHost(&ctx->h_flag, sizeof(int)) == cudaSuccess &&
+         alloc_zero(&ctx->d_anchor, nrhs + 2, ctx->st) == cudaSuccess &&
+         alloc_zero(&ctx->d_loop, 2, ctx->st) == cudaSuccess &&
+         alloc_zero(&ctx->d_hist, CG_WINDOW_MAX, ctx->st) == cudaSuccess &&
+         cudaMallocHost(&ctx->h_anchor, sizeof(double) * (nrhs + 2)) == cudaSuccess &&
+         cudaMallocHost(&ctx->h_loop, sizeof(int) * 2) == cudaSuccess &&
+         cudaMallocHost(&ctx->h_hist, sizeof(double) * CG_WINDOW_MAX) == cudaSuccess;
     if (ok && ctx->implicit) {
       for (double** q : {&ctx->iu_prev, &ctx->iu, &ctx->iu_next, &ctx->ig, &ctx->ir, &ctx->ip, &ctx->iq, &ctx->iacc})
         ok = ok && alloc_zero(q, n, ctx->st) == cudaSuccess;
@@ -1847,6 +2122,12 @@ void ewh_destroy(ewh_ctx* ctx) {
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
   if (ctx->h_act) cudaFreeHost(ctx->h_act);
   if (ctx->h_flag) cudaFreeHost(ctx->h_flag);
+  cudaFree(ctx->d_anchor);
+  cudaFree(ctx->d_loop);
+  cudaFree(ctx->d_hist);
+  if (ctx->h_anchor) cudaFreeHost(ctx->h_anchor);
+  if (ctx->h_loop) cudaFreeHost(ctx->h_loop);
+  if (ctx->h_hist) cudaFreeHost(ctx->h_hist);
   for (auto& t : ctx->pending) {
     cudaEventDestroy(t.e0);
     cudaEventDestroy(t.e1);
@@ -1885,12 +2166,13 @@ ewh_status ewh_get_info(const ewh_ctx* ctx, ewh_problem_info* info) {
   for (int a = 0; a < 3; ++a) info->nu[a] = ctx->g.nu[a];
   info->kernel_variant[0] = ctx->w64.variant;
   info->kernel_variant[1] = ctx->w32.variant;
-  for (int k = 0; k < 8; ++k) info->resident[k] = -1;
+  for (int k = 0; k < 10; ++k) info->resident[k] = -1;
   const int v = ctx->w32.variant;
   if (is_resident_variant(v)) {
     const ResidentPlan& p = ctx->w32.rplan[v - VARIANT_RESIDENT];
-    const int r[8] = {p.shape, p.px, p.py, p.bx, p.ex, p.by, RS_SHAPE_THREADS[p.shape], RS_SHAPE_PAIRS[p.shape]};
-    for (int k = 0; k < 8; ++k) info->resident[k] = r[k];
+    const int r[10] = {p.shape, p.px, p.py, p.bx, p.ex, p.by, RS_SHAPE_THREADS[p.shape], RS_SHAPE_PAIRS[p.shape],
+                       p.rg, p.groups};
+    for (int k = 0; k < 10; ++k) info->resident[k] = r[k];
   }
   return EWH_OK;
 }
@@ -2058,6 +2340,7 @@ void ewh_batch_destroy(ewh_batch* b) {
   if (!b) return;
   if (b->master) cudaStreamSynchronize(b->master);
   if (b->iter_graph) cudaGraphExecDestroy(b->iter_graph);
+  if (b->loop_graph) cudaGraphExecDestroy(b->loop_graph);
   for (auto c : b->p) ewh_destroy(c);
   for (auto e : b->joins) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -2088,7 +2371,6 @@ ewh_status ewh_batch_create(const ewh_problem* probs, int nprob, void* cuda_stre
       g_create_error = m;
       return s;
     }
-    c->allow_resident = false;  // member solves run as concurrent graph branches
     b->p.push_back(c);
   }
   b->joins.resize(nprob, nullptr);

@@ -115,7 +115,7 @@ struct WaveFields {
   const T* frho;   // f / rho per rhs and component, or nullptr (S apply)
   T* sigma;        // order-4 stress scratch (dim*(dim+1)/2 fields per rhs) or nullptr
   const T* met = nullptr;  // mapped grids: 4 planes (y_r, -x_r, -y_q, x_q) of one padded component
-  const ZmPlan* zm = nullptr;  // 3D order 4, FP32: plan of the fused z-march step (host pointer)
+  const ZmPlan* zm = nullptr;  // order 4, FP32: plan of the fused marching step (host pointer)
 };
 
 // ---- launchers (ewh_stencil.cu) -------------------------------------------
@@ -156,6 +156,12 @@ cudaError_t launch_cg_xr_update(const Geom& g, const double* mw, const double* a
 //   rr_new = sum part ; beta = rr_new / rr ; rr = rr_new ; res = sqrt(rr_new / bb)
 cudaError_t launch_cg_beta(int nrhs, const double* part, int nblk, double* rr, const double* bb,
                            double* beta, double* res, const int* active, cudaStream_t st);
+//   device-side loop control after an iteration (a while-conditional graph
+//   node): ++ctl[0], hist[ctl[0] - 1] = max active res, continue unless a
+//   replacement is due (anchor: nrhs anchors, then tol and drop), the
+//   breakdown flag is set or ctl[0] reaches ctl[1]
+cudaError_t launch_cg_control(cudaGraphConditionalHandle h, int nrhs, const double* res, const int* active,
+                              const double* anchor, const int* flags, int* ctl, double* hist, cudaStream_t st);
 //   after a residual replacement: beta *= dot / rr ; rr = dot ; res = sqrt(dot / bb)
 cudaError_t launch_cg_replace(int nrhs, const double* dot, double* rr, double* beta, double* res, const double* bb,
                               cudaStream_t st);
@@ -190,6 +196,8 @@ struct ResidentPlan {
   int ex = 0;          // width of the first block along x (the x-closure columns cost more, so the
                        // first and last blocks along x are narrower); the last is the remainder
   size_t smem = 0;     // dynamic shared memory per CTA in bytes
+  int rg = 1;          // right-hand sides per cooperative launch (rg x px x py CTAs, all co-resident)
+  int groups = 1;      // launches per wave solve, one after another
 };
 // Partition of g for the current device and a CTA shape (ok = 0 when g does
 // not fit on chip).

@@ -305,6 +305,54 @@ cudaError_t launch_cg_beta(int nrhs, const double* part, int nblk, double* rr, c
   return cudaGetLastError();
 }
 
+// Device-side control of the CG loop: a while-conditional graph node runs
+// one iteration per pass, this kernel last.  It counts the iteration
+// (ctl[0]), records its history entry hist[it - 1] (the largest recursive
+// relative residual of the active right-hand sides) and ends the loop when
+// the host has to act: an FP64 residual replacement is due for an active rhs
+// (its residual reached tol = anchor[nrhs], or fell by the factor drop =
+// anchor[nrhs + 1] below its anchor), the breakdown flag is set, or the
+// window of ctl[1] iterations is used up.
+// The host takes the same decisions from the same scalars, so the iterates
+// are those of the host-driven loop.
+__global__ void cg_control_kernel(cudaGraphConditionalHandle h, int nrhs, const double* __restrict__ res,
+                                  const int* __restrict__ active, const double* __restrict__ anchor,
+                                  const int* __restrict__ flags, int* __restrict__ ctl, double* __restrict__ hist) {
+  const double tol = anchor[nrhs], drop = anchor[nrhs + 1];
+  __shared__ double s_max[RED_THREADS];
+  __shared__ int s_rep[RED_THREADS];
+  double m = 0.0;
+  int rep = 0;
+  for (int k = threadIdx.x; k < nrhs; k += blockDim.x)
+    if (active[k]) {
+      const double r = res[k];
+      m = fmax(m, r);
+      rep |= (r <= tol || (drop > 0.0 && r <= drop * anchor[k])) ? 1 : 0;
+    }
+  s_max[threadIdx.x] = m;
+  s_rep[threadIdx.x] = rep;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s_max[threadIdx.x] = fmax(s_max[threadIdx.x], s_max[threadIdx.x + w]);
+      s_rep[threadIdx.x] |= s_rep[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int it = ctl[0] + 1;
+    ctl[0] = it;
+    hist[it - 1] = s_max[0];
+    const bool stop = s_rep[0] != 0 || (*flags & 1) != 0 || it >= ctl[1];
+    cudaGraphSetConditional(h, stop ? 0u : 1u);
+  }
+}
+cudaError_t launch_cg_control(cudaGraphConditionalHandle h, int nrhs, const double* res, const int* active,
+                              const double* anchor, const int* flags, int* ctl, double* hist, cudaStream_t st) {
+  cg_control_kernel<<<1, RED_THREADS, 0, st>>>(h, nrhs, res, active, anchor, flags, ctl, hist);
+  return cudaGetLastError();
+}
+
 __global__ void axpby_kernel(long long n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = a * x[i] + b * y[i];

@@ -1233,11 +1233,14 @@ cudaError_t launch_minvK(const Geom& g, int order, const T* u, T* out, const T* 
 }
 
 // ---------------------------------------------------------------------------
-// Order 4 (SBP), 2D, FP32, one right-hand side: every time level of a wave
-// solve in ONE cooperative launch with the state held on chip.
+// Order 4 (SBP), 2D, FP32: every time level of a wave solve in ONE
+// cooperative launch per group of right-hand sides, with the state held on
+// chip.
 //
-// One CTA of NT threads per SM owns a wx x wy block of nodes (every block
-// at least 8 x 8, so SBP closure reaches stay inside the halos).  Its nodes
+// One CTA of NT threads per SM owns a wx x wy block of nodes of one
+// right-hand side (every block at least 8 x 8, so SBP closure reaches stay
+// inside the halos); a launch holds px x py blocks of each of rg right-hand
+// sides, and the groups of a multi-rhs context run one launch after another.  Its nodes
 // on central rows and columns (x, y in [4, n - 5]) form a rectangle, done in
 // pairs along x with no per-node test; the others (within 4 nodes of a side:
 // SBP closures, boundary terms, Dirichlet nodes) are special and take a pass
@@ -1323,6 +1326,7 @@ __device__ __forceinline__ bool rs_closure(int x, int n) { return x < 4 || x > n
 
 struct ResidentShape {
   int px, bx, by, ex;  // CTAs along x; interior block width; block height; first block width
+  int nb;              // CTAs per right-hand side (px * py): CTA b holds block b % nb of rhs b / nb
 };
 
 // The shared-memory layout is fixed at compile time (so every stencil and
@@ -1562,13 +1566,24 @@ __device__ __forceinline__ void rs_update(int ix, int iy, float au, float av, co
 }
 
 template <int NT, int NP>
-__global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShape sh, ResidentIO io) {
+__global__ void __launch_bounds__(NT, 1) step2d_o4_resident(Geom g, ResidentShape sh, ResidentIO iop) {
   if (g.dim != 2) return;
   __shared__ int s_ok;
-  const unsigned long long wait_ns = *reinterpret_cast<const unsigned long long*>(io.bar + 2);
+  const unsigned long long wait_ns = *reinterpret_cast<const unsigned long long*>(iop.bar + 2);
   const int n0 = g.n[0], n1 = g.n[1];
-  const int cx = blockIdx.x % sh.px;
-  const int X0 = cx == 0 ? 0 : sh.ex + (cx - 1) * sh.bx, Y0 = (blockIdx.x / sh.px) * sh.by;
+  // this CTA's right-hand side (of the launch's group) and block
+  const int rloc = blockIdx.x / sh.nb, bid = blockIdx.x - rloc * sh.nb;
+  ResidentIO io = iop;
+  {
+    const long long ro = (long long)rloc * 2 * g.field;
+    io.u0 += ro;
+    io.xbuf0 += ro;
+    io.xbuf1 += ro;
+    io.acc += ro;
+    if (io.frho) io.frho += ro;
+  }
+  const int cx = bid % sh.px;
+  const int X0 = cx == 0 ? 0 : sh.ex + (cx - 1) * sh.bx, Y0 = (bid / sh.px) * sh.by;
   const int wx = cx == 0 ? sh.ex : min(sh.bx, n0 - X0), wy = min(sh.by, n1 - Y0);
   // u: [RS_BYMAX + 8][RS_UX] per component, block node (0, 0) at (4, 4);
   // stresses: [RS_BYMAX + 4][RS_SX], block node (0, 0) at (2, 2);
@@ -1843,7 +1858,7 @@ static cudaError_t resident_prepare_shape(int shape, int smem_max, size_t smem, 
 
 ResidentPlan plan_resident_o4(const Geom& g, int shape) {
   ResidentPlan best;
-  if (g.dim != 2 || g.nrhs != 1 || g.field >= (1LL << 31) || shape < 0 || shape >= RS_SHAPES) return best;
+  if (g.dim != 2 || g.nrhs < 1 || g.field >= (1LL << 31) || shape < 0 || shape >= RS_SHAPES) return best;
   int dev = 0, sms = 0, smem_max = 0, coop = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -1852,6 +1867,17 @@ ResidentPlan plan_resident_o4(const Geom& g, int shape) {
     cudaGetLastError();
     return best;
   }
+  // every CTA of a launch must be resident at once
+  int per_sm = 0;
+  const cudaError_t e = resident_prepare_shape(shape, smem_max, resident_smem(), &per_sm);
+  const bool verbose = getenv("EWH_VERBOSE") != nullptr;
+  if (e != cudaSuccess || per_sm < 1) {
+    if (verbose) fprintf(stderr, "ewh: resident shape %d unusable (%s)\n", shape, cudaGetErrorString(e));
+    cudaGetLastError();
+    return best;
+  }
+  const int ctas = per_sm * sms;  // co-resident CTAs of one launch
+  const int R = g.nrhs;
   const long long cap = 2LL * RS_SHAPE_THREADS[shape] * RS_SHAPE_PAIRS[shape];
   const int n0 = g.n[0], n1 = g.n[1];
   // Blocks that hold x-closure columns (the first and last along x) take
@@ -1859,8 +1885,14 @@ ResidentPlan plan_resident_o4(const Geom& g, int shape) {
   // they get proportionally fewer columns, so all CTAs reach each barrier
   // together.
   constexpr double RS_EDGE_COST = 1.1;
+  // A level costs a CTA about its tile work plus a fixed part (the barrier,
+  // the halo exchange) worth RS_LEVEL_FIXED tile positions.  With several
+  // right-hand sides, each launch carries a group of rg of them (rg x px x py
+  // CTAs, all co-resident) and the groups run one after another: the cost is
+  // the number of groups times the slowest CTA's level.
+  constexpr double RS_LEVEL_FIXED = 3000.0;
   double best_cost = -1.0;
-  for (int px = 1; px <= sms && px <= n0 / 8; ++px) {
+  for (int px = 1; px <= ctas && px <= n0 / 8; ++px) {
     int bx, ex, last;
     if (px == 1) {
       bx = ex = last = n0;
@@ -1871,7 +1903,7 @@ ResidentPlan plan_resident_o4(const Geom& g, int shape) {
     }
     if (ex < 8 || last < 8 || bx > RS_BXMAX || ex > RS_BXMAX || last > RS_BXMAX) continue;
     const int wmax = std::max(bx, std::max(ex, last));
-    for (int py = 1; px * py <= sms && py <= n1 / 8; ++py) {
+    for (int py = 1; px * py <= ctas && py <= n1 / 8; ++py) {
       const int by = (n1 + py - 1) / py;
       const int pya = (n1 + by - 1) / by;
       if (n1 - (pya - 1) * by < 8) continue;
@@ -1894,8 +1926,13 @@ ResidentPlan plan_resident_o4(const Geom& g, int shape) {
       if (sm > (size_t)smem_max) continue;
       // per-CTA work (u tile + stress tile) of the slowest block
       auto work = [&](int w) { return (double)(w + 2 * RS_HU) * (by + 2 * RS_HU) + (double)(w + 2 * RS_HS) * (by + 2 * RS_HS); };
-      const double cost = px == 1 ? work(bx) * RS_EDGE_COST
-                                  : std::max(work(bx), RS_EDGE_COST * work(std::max(ex, last)));
+      const double level = px == 1 ? work(bx) * RS_EDGE_COST
+                                   : std::max(work(bx), RS_EDGE_COST * work(std::max(ex, last)));
+      const int nb = px * pya;
+      const int rg0 = std::min(R, ctas / nb);
+      if (rg0 < 1) continue;
+      const int groups = (R + rg0 - 1) / rg0;
+      const double cost = groups * (level + RS_LEVEL_FIXED);
       if (best_cost < 0 || cost < best_cost) {
         best_cost = cost;
         best.ok = 1;
@@ -1906,31 +1943,25 @@ ResidentPlan plan_resident_o4(const Geom& g, int shape) {
         best.ex = ex;
         best.by = by;
         best.smem = sm;
+        best.groups = groups;
+        best.rg = (R + groups - 1) / groups;  // balanced groups
       }
     }
   }
   if (!best.ok) return best;
-  // every CTA must be resident at once
-  int per_sm = 0;
-  const cudaError_t e = resident_prepare_shape(shape, smem_max, best.smem, &per_sm);
-  const bool verbose = getenv("EWH_VERBOSE") != nullptr;
-  if (e != cudaSuccess || (long long)per_sm * sms < (long long)best.px * best.py) {
-    if (verbose)
-      fprintf(stderr, "ewh: resident shape %d unusable (%s, %d CTA/SM, %d x %d CTAs)\n", shape, cudaGetErrorString(e),
-              per_sm, best.px, best.py);
-    cudaGetLastError();
-    return ResidentPlan{};
-  }
   if (verbose)
-    fprintf(stderr, "ewh: resident shape %d: %d x %d CTAs of %d (first %d) x %d nodes, %zu B shared\n", shape, best.px,
-            best.py, best.bx, best.ex, best.by, best.smem);
+    fprintf(stderr,
+            "ewh: resident shape %d: %d x %d CTAs of %d (first %d) x %d nodes per rhs, %d rhs per launch in %d "
+            "launches, %zu B shared\n",
+            shape, best.px, best.py, best.bx, best.ex, best.by, best.rg, best.groups, best.smem);
   return best;
 }
 
 template <int NT, int NP>
-static cudaError_t resident_launch(const Geom& g, const ResidentPlan& p, const ResidentIO& io, cudaStream_t st) {
+static cudaError_t resident_launch(const Geom& g, const ResidentPlan& p, const ResidentIO& io, int nr,
+                                   cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(p.px * p.py);
+  cfg.gridDim = dim3(nr * p.px * p.py);
   cfg.blockDim = dim3(NT);
   cfg.dynamicSmemBytes = p.smem;
   cfg.stream = st;
@@ -1939,20 +1970,36 @@ static cudaError_t resident_launch(const Geom& g, const ResidentPlan& p, const R
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  ResidentShape sh{p.px, p.bx, p.by, p.ex};
+  ResidentShape sh{p.px, p.bx, p.by, p.ex, p.px * p.py};
   return cudaLaunchKernelEx(&cfg, step2d_o4_resident<NT, NP>, g, sh, io);
 }
 
+// The groups of right-hand sides one after another, each one cooperative
+// launch (its barrier words zeroed first).
 cudaError_t launch_resident_o4(const Geom& g, const ResidentPlan& p, const ResidentIO& io, cudaStream_t st) {
-  if (!p.ok || g.dim != 2 || g.nrhs != 1 || io.nsteps < 1) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(io.bar, 0, 2 * sizeof(unsigned), st);
-  if (e != cudaSuccess) return e;
-  switch (p.shape) {
-    case 0: return resident_launch<RS_SHAPE_THREADS[0], RS_SHAPE_PAIRS[0]>(g, p, io, st);
-    case 1: return resident_launch<RS_SHAPE_THREADS[1], RS_SHAPE_PAIRS[1]>(g, p, io, st);
-    case 2: return resident_launch<RS_SHAPE_THREADS[2], RS_SHAPE_PAIRS[2]>(g, p, io, st);
-    default: return cudaErrorInvalidValue;
+  if (!p.ok || g.dim != 2 || io.nsteps < 1 || p.rg < 1 || (long long)p.rg * p.groups < g.nrhs)
+    return cudaErrorInvalidValue;
+  for (int k = 0; k < p.groups; ++k) {
+    const int r0 = k * p.rg, nr = std::min(p.rg, g.nrhs - r0);
+    if (nr < 1) break;
+    ResidentIO gi = io;
+    const long long ro = (long long)r0 * 2 * g.field;
+    gi.u0 += ro;
+    gi.xbuf0 += ro;
+    gi.xbuf1 += ro;
+    gi.acc += ro;
+    if (gi.frho) gi.frho += ro;
+    cudaError_t e = cudaMemsetAsync(io.bar, 0, 2 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    switch (p.shape) {
+      case 0: e = resident_launch<RS_SHAPE_THREADS[0], RS_SHAPE_PAIRS[0]>(g, p, gi, nr, st); break;
+      case 1: e = resident_launch<RS_SHAPE_THREADS[1], RS_SHAPE_PAIRS[1]>(g, p, gi, nr, st); break;
+      case 2: e = resident_launch<RS_SHAPE_THREADS[2], RS_SHAPE_PAIRS[2]>(g, p, gi, nr, st); break;
+      default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
   }
+  return cudaSuccess;
 }
 
 template cudaError_t launch_step<float>(const Geom&, int, const WaveFields<float>&, StepMode,

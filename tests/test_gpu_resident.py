@@ -1,7 +1,8 @@
-"""The on-chip resident wave solve (2D, order-4 SBP, FP32 stencil, one
-right-hand side: every leapfrog level of S in one cooperative launch, the
-state in shared memory and registers, halos exchanged through global memory
-at one grid barrier per level) against the oracle.
+"""The on-chip resident wave solve (2D, order-4 SBP, FP32 stencil: every
+leapfrog level of S in one cooperative launch per group of right-hand sides,
+the state in shared memory and registers, halos exchanged through global
+memory at one grid barrier per level) against the oracle, for one and
+several right-hand sides and for batch members.
 
 EWH_STEP2D_O4=r<k> selects CTA shape k (1024 x 7, 768 x 9, 512 x 14 threads
 x nodes per thread) when the grid fits it; each test checks that the chosen
@@ -135,29 +136,108 @@ def test_resident_matches_split_kernels(monkeypatch):
     assert rel_err(b, a) < 2 * tol32(nt)
 
 
-def test_resident_not_used_for_batches_or_several_rhs(monkeypatch):
-    """Batch members (concurrent graph branches) and multi-rhs contexts keep
-    the per-level kernels."""
+@pytest.mark.parametrize("shape", [0, 2])
+@pytest.mark.parametrize("grid,bc,nrhs", [([45, 19], [D, D, D, F], 3), ([70, 131], [F, D, D, F], 2)],
+                         ids=["45x19r3", "70x131r2"])
+def test_resident_several_rhs_match_oracle(grid, bc, nrhs, shape, monkeypatch):
+    """A multi-rhs context on chip: one cooperative launch carries the blocks
+    of every right-hand side; S v and Pi 0 (forced, eq. qoper) of each rhs
+    against the oracle."""
+    from paper_2205_12344_gb300 import _lib as L
+    monkeypatch.setenv("EWH_STEP2D_O4", "r%d" % shape)
+    p = inputs.small_problem(2, grid, 4, bc + [0, 0], seed=45 + shape, nrhs=nrhs)
+    s = O.build_system(p)
+    v = inputs.random_vectors(p, 1, 46)[0]
+    want = oracle_all_rhs(s, lambda ss, x, r: O.apply_S(ss, x, r), v)
+    want0 = np.concatenate([O.apply_Pi0(s, r) for r in range(nrhs)])
+    with _fp32(p) as wh:
+        got = to_np(wh.apply_S(v))
+        got0 = to_np(wh.apply_Pi0())
+        assert _variant(wh) == VARIANT_RESIDENT + shape
+        plan = list(L.ewh_get_info(wh.ctx).resident)
+    assert plan[8] == nrhs and plan[9] == 1  # every rhs in one launch
+    assert rel_err(got, want) < tol32(s.nt)
+    assert rel_err(got0, want0) < tol32(s.nt)
+
+
+@pytest.fixture(scope="module")
+def member256_nt6():
+    """A batch member's size: layered 256^2 with 22 shots, w raised so that
+    N_t = 6; one random input vector per shot."""
+    shots = [0.1 + 0.11 * k for k in range(22)]
+    p = inputs.cfg_layered_2d(nu=256, order=4, nrhs=22, shot_x=shots)
+    dtc = O.cfl_dt(2, 4, p.h, p.cfl, p.rho, p.lam, p.mu)
+    p.omega = 2 * math.pi / (5.5 * dtc)
+    v = inputs.random_vectors(p, 1, 53)[0]
+    return p, v
+
+
+def test_resident_rhs_groups_match_split_and_oracle(member256_nt6, monkeypatch):
+    """22 right-hand sides of 256^2 do not fit one co-resident launch: they
+    run as groups of launches, one after another.  Every node of every rhs
+    against the oracle-checked split kernels, and nodes of the first and last
+    rhs (by the free top, a Dirichlet side, a CTA seam) against the oracle on
+    their domains of dependence."""
+    from paper_2205_12344_gb300 import _lib as L
+    p, v = member256_nt6
+    monkeypatch.setenv("EWH_STEP2D_O4", "split")
+    with _fp32(p) as wh:
+        a = to_np(wh.apply_S(v))
+    monkeypatch.setenv("EWH_STEP2D_O4", "r1")
+    with _fp32(p) as wh:
+        b = to_np(wh.apply_S(v))
+        info = L.ewh_get_info(wh.ctx)
+        assert info.kernel_variant[1] == VARIANT_RESIDENT + 1 and info.nt == 6
+        plan = list(info.resident)
+    rg, groups = plan[8], plan[9]
+    assert groups >= 2 and rg * groups >= p.nrhs and rg * (groups - 1) < p.nrhs, plan
+    assert rel_err(b, a) < 2 * tol32(6)
+    nn = p.n_nodes()
+    n1 = 2 * nn
+    idx = inputs.unknown_index(p)
+    by = plan[5]
+    scale = np.abs(b).max()
+    for r in (0, p.nrhs - 1):
+        pr = inputs.cfg_layered_2d(nu=256, order=4, nrhs=1, shot_x=[0.1 + 0.11 * r])
+        pr.omega = p.omega
+        vr = v[r * n1:(r + 1) * n1]
+        for node in [(128, p.n[1] - 2), (1, 100), (200, by - 1), (200, by)]:
+            want = window_sample(pr, 6, vr, node, reach=4)
+            g = np.array([b[r * n1 + c * nn + idx[node[1], node[0]]] for c in range(2)])
+            assert np.abs(g - want).max() <= tol32(6) * scale, (r, node, g, want)
+
+
+def test_resident_batch_members_run_serially_and_match_single(monkeypatch):
+    """Batch members on chip: the batch graph runs their cooperative launches
+    one after another; every member's S v equals the same problem alone
+    (bitwise) and the oracle, and the batched FP32 solve reaches an FP64
+    residual the oracle confirms."""
     monkeypatch.setenv("EWH_STEP2D_O4", "r0")
     from paper_2205_12344_gb300 import _lib as L
     from paper_2205_12344_gb300.api import WaveHoltzBatch
-    p2 = inputs.small_problem(2, [30, 30], 4, [D, D, D, F, 0, 0], seed=45, nrhs=2)
-    s2 = O.build_system(p2)
-    v2 = inputs.random_vectors(p2, 1, 46)[0]
-    with _fp32(p2) as wh:
-        got = to_np(wh.apply_S(v2))
-        assert _variant(wh) < VARIANT_RESIDENT
-    want = oracle_all_rhs(s2, lambda ss, x, r: O.apply_S(ss, x, r), v2)
-    assert rel_err(got, want) < tol32(s2.nt)
-    probs = [inputs.small_problem(2, [30, 30], 4, [D, D, D, F, 0, 0], seed=47 + k) for k in range(2)]
-    b = WaveHoltzBatch(probs, precision="fp32")
-    try:
-        b.solve(tol=1e-6, maxit=20, raise_on_error=False)
-        for k in range(2):
-            ctx = L.ewh_batch_member(b.b, k)
-            assert L.ewh_get_info(ctx).kernel_variant[1] < VARIANT_RESIDENT
-    finally:
-        b.close()
+    probs = [inputs.small_problem(2, [40, 34], 4, [D, D, D, F, 0, 0], seed=42, nrhs=2, omega=6.0),
+             inputs.small_problem(2, [30, 30], 4, [D, D, D, F, 0, 0], seed=47, omega=5.0)]
+    vs = [inputs.random_vectors(p, 1, 48 + k)[0] for k, p in enumerate(probs)]
+    with WaveHoltzBatch(probs, "fp32") as wb:
+        outs = [to_np(o) for o in wb.apply_S(vs)]
+        for k in range(len(probs)):
+            assert L.ewh_get_info(L.ewh_batch_member(wb.b, k)).kernel_variant[1] == VARIANT_RESIDENT
+        xs, infos = wb.solve(tol=1e-7, maxit=4000)
+    for p, v, o, x, inf in zip(probs, vs, outs, xs, infos):
+        with _fp32(p) as wh:
+            single = to_np(wh.apply_S(v))
+            assert _variant(wh) == VARIANT_RESIDENT
+        assert np.array_equal(o, single)
+        s = O.build_system(p)
+        assert rel_err(o, oracle_all_rhs(s, lambda ss, xx, r: O.apply_S(ss, xx, r), v)) < tol32(s.nt)
+        assert inf.status == 0 and inf.rel_res <= 1e-7
+        n = s.K.shape[0]
+        x = to_np(x)
+        for r in range(p.nrhs):
+            b = O.apply_Pi0(s, r)
+            xr = x[r * n:(r + 1) * n]
+            res = b - (xr - O.apply_S(s, xr, r))
+            assert math.sqrt(O.mdot(s, res, res) / O.mdot(s, b, b)) <= 1.01e-7
 
 
 @pytest.mark.parametrize("shape", [0, 2])
