@@ -234,15 +234,21 @@ ewh_status ewh_residual_history(const ewh_ctx* ctx, double* out, int cap, int* c
 long long ewh_kernel_launches(const ewh_ctx* ctx);
 
 /* Device-time accounting of the leapfrog steps.  Every wave solve (S or Pi 0
- * apply) is bracketed by CUDA events on the context's stream; the elapsed
- * times are accumulated per precision.  Index 0 = FP64, 1 = FP32. */
+ * apply) launched by the host is bracketed by CUDA events on the context's
+ * stream; the elapsed times are accumulated per precision.  The S applies of
+ * CG iterations under device control (a window of iterations in one graph
+ * launch, see ewh_solve) are counted apart, untimed.  Index 0 = FP64,
+ * 1 = FP32. */
 typedef struct {
-  double wave_ms[2];     /* device milliseconds spent in wave solves */
+  double wave_ms[2];     /* device milliseconds spent in event-timed wave solves */
   long long steps[2];    /* leapfrog steps (time levels) those solves covered */
-  long long waves[2];    /* number of wave solves */
+  long long waves[2];    /* number of event-timed wave solves */
   long long launches;    /* kernel launches issued (as ewh_kernel_launches) */
   long long grid_wait_timeouts; /* on-chip wave solves whose grid-barrier wait
                                    gave up (see ewh_set_grid_wait) */
+  long long loop_steps[2];  /* leapfrog steps of the wave solves run inside
+                               device-controlled CG windows (not timed) */
+  long long loop_waves[2];  /* number of those wave solves */
 } ewh_stats;
 
 /* Fill *out (synchronises the context's stream first). */

@@ -37,7 +37,8 @@ class ewh_solve_info(ctypes.Structure):
 class ewh_stats(ctypes.Structure):
     _fields_ = [("wave_ms", ctypes.c_double * 2), ("steps", ctypes.c_longlong * 2),
                 ("waves", ctypes.c_longlong * 2), ("launches", ctypes.c_longlong),
-                ("grid_wait_timeouts", ctypes.c_longlong)]
+                ("grid_wait_timeouts", ctypes.c_longlong), ("loop_steps", ctypes.c_longlong * 2),
+                ("loop_waves", ctypes.c_longlong * 2)]
 
 
 class ewh_problem(ctypes.Structure):

@@ -187,6 +187,13 @@ class WaveHoltzBatch:
         L.ewh_batch_apply_S(self.b, vin, vout)
         return vout
 
+    def apply_Pi0(self):
+        """b = Pi 0 of every member (each member context's own apply)."""
+        out = self._vecs()
+        for k, o in enumerate(out):
+            L.ewh_apply_Pi0(L.ewh_batch_member(self.b, k), o)
+        return out
+
     def solve(self, tol=1e-8, maxit=100000, raise_on_error=True):
         out = self._vecs()
         infos = L.ewh_batch_solve(self.b, tol, maxit, out, raise_on_error=raise_on_error)

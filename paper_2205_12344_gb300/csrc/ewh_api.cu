@@ -63,6 +63,8 @@ struct Wave {
 // step-kernel variants of the 2D order-4 FP32 solve beyond the launcher's
 // own (split tiles 0..3, fused 4): 5 + shape = resident solve of that shape
 constexpr int VARIANT_RESIDENT = 5;
+// least nodes per CTA block of a batch member's on-chip solve (resident_ok)
+constexpr long long RS_BATCH_MIN_BLOCK = 2048;
 // longest window of CG iterations under device control between host polls
 constexpr int CG_WINDOW_MAX = 256;
 static_assert(VARIANT_RESIDENT + RS_SHAPES == YM_VARIANT, "2D order-4 variants: split 0..3, fused 4, resident, y-march");
@@ -110,6 +112,7 @@ struct ewh_ctx {
   long long launches = 0;
   // implicit scheme (Section 4.4; FP64, dense unknown layout): level vectors,
   // inner-solve vectors, f/rho, device scalars of the inner CG
+  bool batch_member = false;  // member of an ewh_batch (see resident_ok)
   int implicit = 0;
   double alpha = 2.0;
   double *iu_prev = nullptr, *iu = nullptr, *iu_next = nullptr, *ig = nullptr, *ir = nullptr, *ip = nullptr,
@@ -129,6 +132,8 @@ struct ewh_ctx {
   long long wave_steps[2] = {0, 0};
   long long wave_count[2] = {0, 0};
   long long grid_timeouts_base = 0;  // grid-wait give-ups counted before the last ewh_reset_stats
+  long long loop_steps[2] = {0, 0};   // levels / wave solves inside device-controlled CG windows
+  long long loop_waves[2] = {0, 0};
 };
 
 namespace {
@@ -347,7 +352,7 @@ std::string tune_key(const ewh_ctx* ctx) {
   for (auto& ch : name)
     if (ch == '"' || ch == ' ') ch = '_';
   const Geom& g = ctx->g;
-  return name + "|v4" + (g.mapped ? "|map" : "") + "|d" + std::to_string(g.dim) +
+  return name + "|v4" + (ctx->batch_member ? "b" : "") + (g.mapped ? "|map" : "") + "|d" + std::to_string(g.dim) +
          "|o" + std::to_string(ctx->order) + "|" +
          (sizeof(T) == 8 ? "f64" : "f32") + "|" + std::to_string(g.n[0]) + "x" + std::to_string(g.n[1]) + "x" +
          std::to_string(g.n[2]) + "|r" + std::to_string(g.nrhs);
@@ -356,11 +361,18 @@ std::string tune_key(const ewh_ctx* ctx) {
 // Resident variant v usable by this context?  (FP32 2D order 4, a
 // partition that fits on chip, EWH_RESIDENT != 0.)
 template <typename T>
-bool resident_ok(const ewh_ctx* ctx, const Wave<T>& w, int v) {
+bool resident_ok(const ewh_ctx* ctx, const Wave<T>& w, int v, bool named = false) {
   if (sizeof(T) != 4 || !is_resident_variant(v)) return false;
   const char* e = getenv("EWH_RESIDENT");
   if (e && e[0] == '0') return false;
-  return w.rplan[v - VARIANT_RESIDENT].ok != 0;
+  const ResidentPlan& p = w.rplan[v - VARIANT_RESIDENT];
+  if (!p.ok) return false;
+  // A batch runs its members' cooperative launches one after another, so a
+  // member goes on chip only when its blocks are large enough that its own
+  // launches keep the GPU busy; smaller members run their per-level kernels
+  // in concurrent branches.  (EWH_STEP2D_O4=r<k> names the shape regardless.)
+  if (ctx->batch_member && !named && (long long)p.bx * p.by < RS_BATCH_MIN_BLOCK) return false;
+  return true;
 }
 
 // One cooperative launch running nsteps levels of the wave solve on chip.
@@ -413,7 +425,7 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
   w.fallback = 0;
   if (force && force[0] == 'r') {  // EWH_STEP2D_O4=r, r0, r1, r2: resident solve of that CTA shape
     const int k = (force[1] >= '0' && force[1] < '0' + RS_SHAPES) ? force[1] - '0' : 0;
-    if (resident_ok<T>(ctx, w, VARIANT_RESIDENT + k)) {
+    if (resident_ok<T>(ctx, w, VARIANT_RESIDENT + k, true)) {
       w.variant = VARIANT_RESIDENT + k;
       return;
     }
@@ -1101,6 +1113,8 @@ ewh_status run_cg(ewh_ctx* ctx, double* x, double* r, double tol, int maxit, dou
       const int it = ctx->h_loop[0];
       if (it < 1 || it > limit) return fail(ctx, EWH_ECUDA, "device-controlled CG loop ran no iteration");
       ctx->launches += (long long)it * w.cg_loop_kernels;
+      ctx->loop_steps[sizeof(T) == 4 ? 1 : 0] += (long long)it * ctx->nt * ctx->periods;
+      ctx->loop_waves[sizeof(T) == 4 ? 1 : 0] += it;
       for (int i = 0; i + 1 < it; ++i) {  // iterations that needed no host decision
         ctx->history.push_back(ctx->h_hist[i]);
         ++inf->iters;
@@ -1705,6 +1719,8 @@ ewh_status batch_solve_T(ewh_batch* b, double tol, int maxit, double* const* v_o
         const int it = ctx->h_loop[0];
         if (it < 1) return bfail(b, EWH_ECUDA, "device-controlled batch window ran no iteration");
         b->launches += (long long)it * b->loop_kernels[k];
+        ctx->loop_steps[sizeof(T) == 4 ? 1 : 0] += (long long)it * ctx->nt * ctx->periods;
+        ctx->loop_waves[sizeof(T) == 4 ? 1 : 0] += it;
         for (int i = 0; i + 1 < it; ++i) {  // iterations that needed no host decision
           ctx->history.push_back(ctx->h_hist[i]);
           ++inf[k].iters;
@@ -2371,6 +2387,7 @@ ewh_status ewh_batch_create(const ewh_problem* probs, int nprob, void* cuda_stre
       g_create_error = m;
       return s;
     }
+    c->batch_member = true;
     b->p.push_back(c);
   }
   b->joins.resize(nprob, nullptr);
@@ -2468,6 +2485,8 @@ ewh_status ewh_get_stats(ewh_ctx* ctx, ewh_stats* out) {
     out->wave_ms[k] = ctx->wave_ms[k];
     out->steps[k] = ctx->wave_steps[k];
     out->waves[k] = ctx->wave_count[k];
+    out->loop_steps[k] = ctx->loop_steps[k];
+    out->loop_waves[k] = ctx->loop_waves[k];
   }
   out->launches = ctx->launches;
   out->grid_wait_timeouts = 0;
@@ -2484,7 +2503,9 @@ ewh_status ewh_reset_stats(ewh_ctx* ctx) {
   if (!ctx) return EWH_EINVAL;
   if (cudaStreamSynchronize(ctx->st) != cudaSuccess) return fail(ctx, EWH_ECUDA, "synchronise failed");
   collect_timing(ctx);
-  for (int k = 0; k < 2; ++k) ctx->wave_ms[k] = 0, ctx->wave_steps[k] = 0, ctx->wave_count[k] = 0;
+  for (int k = 0; k < 2; ++k)
+    ctx->wave_ms[k] = 0, ctx->wave_steps[k] = 0, ctx->wave_count[k] = 0, ctx->loop_steps[k] = 0,
+    ctx->loop_waves[k] = 0;
   ctx->launches = 0;
   if (ctx->w32.bar) {
     unsigned n = 0;

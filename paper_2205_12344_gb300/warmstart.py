@@ -3,14 +3,17 @@
 A 4-level convolutional encoder-decoder with skip connections (channels
 32/64/128/128, 3x3 convolutions, leaky ReLU, 2x2 average pooling, nearest
 upsampling) maps per-node features of the medium, the forcing and the
-frequency to a guess y of the solution's shape.  Weights and activations are
-BF16, accumulation FP32; every layer (forward, backward, Adam) runs in
-libewh.so's kernels; PyTorch only provides device memory and the stream.
+frequency -- and the method's own first two vectors, the right-hand side
+b = Pi 0 and S b (eq. amat_sym), which carry the phase of the wave field --
+to a guess y of the solution's shape.  Weights and activations are BF16,
+accumulation FP32; every layer (forward, backward, Adam) runs in libewh.so's
+kernels; PyTorch only provides device memory and the stream.
 
-Use: x0 = alpha * y with alpha = (b, A y)_M / (A y, A y)_M (one extra FP32 S
-apply), which never raises the initial residual above ||b||_M: the plain
-solve stays the fallback and the judge of the result (the solve's stopping
-rule is the FP64 residual, whatever the start).
+Use: x0 = c1 y + c2 b with (c1, c2) minimising ||b - A x0||_M (A = I - S;
+A b = b - S b is known, A y costs one S apply), which never raises the
+initial residual above ||b||_M: the plain solve stays the fallback and the
+judge of the result (the solve's stopping rule is the FP64 residual,
+whatever the start).
 """
 from __future__ import annotations
 
@@ -24,11 +27,12 @@ IN_CH = 16     # input features, zero-padded to the 16-channel granule
 OUT_CH = 16    # head width (the first two channels are the guess)
 
 
-def features(prob):
+def features(prob, b=None, sb=None):
     """Per-unknown-node input features [H, W, IN_CH] (FP32) of a 2D problem
     with Dirichlet sides: log Vs, log(Vp/Vs), log rho, normalised forcing,
-    frequency relative to the 10-points-per-wavelength frequency, and the
-    node coordinates."""
+    frequency relative to the 10-points-per-wavelength frequency, the node
+    coordinates and, when given, b = Pi 0 and S b (solver layout, scaled by
+    the RMS of b)."""
     assert prob.dim == 2 and all(b == 0 for b in prob.bc[:4]), "warm start: 2D, Dirichlet sides"
     sl = (slice(1, -1), slice(1, -1))
     rho, lam, mu = prob.rho[sl], prob.lam[sl], prob.mu[sl]
@@ -49,6 +53,15 @@ def features(prob):
     out[..., 5] = prob.omega / w10 - 0.75
     out[..., 6] = xs
     out[..., 7] = ys
+    if b is not None:
+        bb = np.asarray(b, dtype=np.float64).reshape(2, H, W)
+        rms = math.sqrt(float(np.mean(bb ** 2))) or 1.0
+        out[..., 8] = bb[0] / rms
+        out[..., 9] = bb[1] / rms
+        if sb is not None:
+            s2 = np.asarray(sb, dtype=np.float64).reshape(2, H, W)
+            out[..., 10] = s2[0] / rms
+            out[..., 11] = s2[1] / rms
     return out
 
 
@@ -239,30 +252,39 @@ def guess_to_vector(y_hw2):
 # Data, training and the with/without comparison
 # ---------------------------------------------------------------------------
 
-def make_media(count, nu, seed0, order=2):
+def make_media(count, nu, seed0, order=2, ppw=None):
     """GRF media (log Vs std 0.2, correlation 0.1, Vp = 1.8 Vs, rho = 1) on the
-    unit square with nu^2 unknowns, frequency uniform in [0.5, 1] x the
-    10-points-per-wavelength frequency, a Gaussian source (sigma 2h) at a
-    random interior position."""
+    unit square with nu^2 unknowns, a Gaussian source (sigma 2h) at a random
+    interior position, and a frequency uniform in [0.5, 1] x the
+    10-points-per-wavelength frequency, or (ppw = (lo, hi)) giving a number of
+    points per shortest wavelength uniform in [lo, hi]."""
     from . import inputs
     rng = np.random.default_rng(seed0)
     probs = []
     for k in range(count):
-        scale = float(rng.uniform(0.5, 1.0))
+        if ppw is None:
+            kw = {"omega_scale": float(rng.uniform(0.5, 1.0))}
+        else:
+            kw = {"ppw": float(rng.uniform(ppw[0], ppw[1]))}
         src = (float(rng.uniform(0.2, 0.8)), float(rng.uniform(0.2, 0.8)))
-        probs.append(inputs.cfg_grf_2d(nu=nu, order=order, seed=seed0 + k, omega_scale=scale, src=src))
+        probs.append(inputs.cfg_grf_2d(nu=nu, order=order, seed=seed0 + k, src=src, **kw))
     return probs
 
 
 def solve_all(probs, tol, chunk=16, precision="fp32"):
-    """Reference solutions with the batched solver (FP64 residual <= tol)."""
+    """Solutions with the batched solver (FP64 residual <= tol), and each
+    problem's b = Pi 0 and S b (the network's phase inputs)."""
     from .api import WaveHoltzBatch
-    sols = []
+    sols, bs, sbs = [], [], []
     for i in range(0, len(probs), chunk):
         with WaveHoltzBatch(probs[i:i + chunk], precision) as wb:
+            b = wb.apply_Pi0()
+            sb = wb.apply_S(b)
             xs, infos = wb.solve(tol=tol, maxit=200000, raise_on_error=False)
             sols += [x.cpu().numpy() for x in xs]
-    return sols
+            bs += [x.cpu().numpy() for x in b]
+            sbs += [x.cpu().numpy() for x in sb]
+    return sols, bs, sbs
 
 
 def train(net, feats, targets, epochs, batch, lr=1e-3, seed=0, log=None):
@@ -297,18 +319,32 @@ def predict(net, feat):
     return net.forward(x)[0, :, :, :2].cpu().numpy()
 
 
-def warm_start_vector(wh, y_hw2):
-    """x0 = alpha y, alpha = (b, A y)_M / (A y, A y)_M with the context's S
-    apply (its working precision) and b = Pi 0: the residual of x0 is never
-    larger than that of the zero start."""
+def warm_start_vector(wh, y_hw2, b=None, sb=None):
+    """x0 = c1 y + c2 b, (c1, c2) minimising ||b - A x0||_M over the span of
+    the guess and b (A = I - S with the context's S apply, its working
+    precision; A b = b - S b): the residual of x0 is never larger than that of
+    the zero start, nor than that of the best multiple of b.  Without b, the
+    best multiple of y.  Returns (x0, (c1, c2))."""
     y = guess_to_vector(y_hw2)
     yt = wh._vec(y)
     Ay = yt - wh.apply_S(yt)
-    b = wh.apply_Pi0()
-    num = wh.mdot(b, Ay)[0]
-    den = wh.mdot(Ay, Ay)[0]
-    alpha = num / den if den > 0 else 0.0
-    return (yt * alpha), alpha
+    if b is None:
+        b = wh.apply_Pi0()
+        num = wh.mdot(b, Ay)[0]
+        den = wh.mdot(Ay, Ay)[0]
+        alpha = num / den if den > 0 else 0.0
+        return yt * alpha, (alpha, 0.0)
+    b = wh._vec(b)
+    Ab = b - (wh._vec(sb) if sb is not None else wh.apply_S(b))
+    g11, g12, g22 = wh.mdot(Ay, Ay)[0], wh.mdot(Ay, Ab)[0], wh.mdot(Ab, Ab)[0]
+    r1, r2 = wh.mdot(Ay, b)[0], wh.mdot(Ab, b)[0]
+    det = g11 * g22 - g12 * g12
+    if det > 1e-14 * g11 * g22:
+        c1 = (r1 * g22 - r2 * g12) / det
+        c2 = (r2 * g11 - r1 * g12) / det
+    else:  # y (nearly) parallel to b: the best multiple of b
+        c1, c2 = 0.0, (r2 / g22 if g22 > 0 else 0.0)
+    return yt * c1 + b * c2, (c1, c2)
 
 
 def compare(net, probs, tol, precision="fp32"):
@@ -327,41 +363,83 @@ def compare(net, probs, tol, precision="fp32"):
             torch.cuda.synchronize()
             t_plain = time.perf_counter() - t0
             t0 = time.perf_counter()
-            y = predict(net, features(p))
-            x0, alpha = warm_start_vector(wh, y)
+            b = wh.apply_Pi0()
+            sb = wh.apply_S(b)
+            y = predict(net, features(p, b.cpu().numpy(), sb.cpu().numpy()))
+            x0, coef = warm_start_vector(wh, y, b, sb)
             xw, iw = wh.solve(tol=tol, maxit=200000, x0=x0, raise_on_error=False)
             torch.cuda.synchronize()
             t_warm = time.perf_counter() - t0
-            b = wh.apply_Pi0()
             r0 = b - (x0 - wh.apply_S(x0))
-            rel0 = math.sqrt(wh.mdot(r0, r0)[0] / wh.mdot(b, b)[0])
+            bb = wh.mdot(b, b)[0]
+            rel0 = math.sqrt(wh.mdot(r0, r0)[0] / bb)
+            # the method without the network: the best multiple of b
+            Ab = b - sb
+            cb = wh.mdot(Ab, b)[0] / wh.mdot(Ab, Ab)[0]
+            rb = b - Ab * cb
+            relb = math.sqrt(wh.mdot(rb, rb)[0] / bb)
         rows.append({"iters_plain": i0.iters, "iters_warm": iw.iters, "t_plain": t_plain, "t_warm": t_warm,
-                     "rel_res_x0": rel0, "status": (i0.status, iw.status)})
+                     "rel_res_x0": rel0, "rel_res_b": relb, "coef": coef, "status": (i0.status, iw.status)})
     return rows
 
 
-def run_experiment(n_train=512, n_test=32, nu=256, epochs=30, batch=8, tol=1e-6, seed=0, log=None):
+def run_experiment(n_train=512, n_test=32, nu=256, epochs=30, batch=8, tol=1e-6, seed=0, log=None, order=2,
+                   ppw=None, lr=1e-3):
     """Generate solutions, train the network on the GPU, compare solves."""
     import time
     t0 = time.perf_counter()
-    probs = make_media(n_train + n_test, nu, seed)
-    sols = solve_all(probs[:n_train], tol)
+    probs = make_media(n_train + n_test, nu, seed, order=order, ppw=ppw)
+    sols, bs, sbs = solve_all(probs[:n_train], tol)
     t_gen = time.perf_counter() - t0
-    feats = [features(p) for p in probs[:n_train]]
+    feats = [features(p, b, sb) for p, b, sb in zip(probs[:n_train], bs, sbs)]
     targs = [target(p, v) for p, v in zip(probs[:n_train], sols)]
     net = WarmStartNet(nu, nu, seed=seed)
     t0 = time.perf_counter()
-    hist = train(net, feats, targs, epochs, batch, log=log)
+    hist = train(net, feats, targs, epochs, batch, lr=lr, log=log)
     t_train = time.perf_counter() - t0
     rows = compare(net, probs[n_train:], tol)
     ip = [r["iters_plain"] for r in rows]
     iw = [r["iters_warm"] for r in rows]
     tp = [r["t_plain"] for r in rows]
     tw = [r["t_warm"] for r in rows]
-    return {"n_train": n_train, "n_test": n_test, "nu": nu, "epochs": epochs, "tol": tol,
+    return {"n_train": n_train, "n_test": n_test, "nu": nu, "epochs": epochs, "tol": tol, "order": order,
+            "ppw": ppw, "rel_res_b_mean": float(np.mean([r["rel_res_b"] for r in rows])),
             "seconds_generate": t_gen, "seconds_train": t_train, "loss_first": hist[0], "loss_last": hist[-1],
             "iters_plain_mean": float(np.mean(ip)), "iters_warm_mean": float(np.mean(iw)),
             "iters_plain_median": float(np.median(ip)), "iters_warm_median": float(np.median(iw)),
             "time_plain_mean": float(np.mean(tp)), "time_warm_mean": float(np.mean(tw)),
             "rel_res_x0_mean": float(np.mean([r["rel_res_x0"] for r in rows])),
             "rows": rows}
+
+
+def main(argv=None):
+    """The warm-start experiment from the command line; writes the result as JSON."""
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--n-train", type=int, default=2000)
+    ap.add_argument("--n-test", type=int, default=200)
+    ap.add_argument("--nu", type=int, default=256)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--order", type=int, default=4)
+    ap.add_argument("--ppw", type=float, nargs=2, default=None, help="points per wavelength range")
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--out", default=None, help="JSON file for the result")
+    a = ap.parse_args(argv)
+    import sys
+    res = run_experiment(n_train=a.n_train, n_test=a.n_test, nu=a.nu, epochs=a.epochs, batch=a.batch, tol=a.tol,
+                         seed=a.seed, order=a.order, ppw=tuple(a.ppw) if a.ppw else None, lr=a.lr,
+                         log=lambda m: print(m, file=sys.stderr, flush=True))
+    text = json.dumps(res, indent=1, default=float)
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(text)
+    summary = {k: v for k, v in res.items() if k != "rows"}
+    print(json.dumps(summary, default=float))
+
+
+if __name__ == "__main__":
+    main()

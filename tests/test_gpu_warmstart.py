@@ -61,6 +61,8 @@ def test_warm_start_trains_and_reports_its_gain(record_property):
     res = WS.run_experiment(n_train=48, n_test=6, nu=32, epochs=12, batch=8, tol=1e-6, seed=5)
     assert res["loss_last"] < 0.8 * res["loss_first"]
     assert res["rel_res_x0_mean"] < 1.0
+    # the least-squares start over (guess, b) is never worse than the best multiple of b
+    assert all(r["rel_res_x0"] <= r["rel_res_b"] * 1.001 + 1e-5 for r in res["rows"])  # FP32 S rounding
     assert all(r["status"] == (0, 0) for r in res["rows"])
     for k in ("iters_plain_mean", "iters_warm_mean", "time_plain_mean", "time_warm_mean", "rel_res_x0_mean"):
         record_property(k, res[k])
