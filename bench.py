@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the plain FP64 GPU solve used for the time-to-tol comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 192-system measurement")
+    ap.add_argument("--batch-full-tol", action="store_true",
+                    help="also solve the full 192-system batch to 1e-6 (minutes of GPU time; off by default)")
     ap.add_argument("--batch-iters", type=int, default=100, help="batched CG iterations timed")
     ap.add_argument("--no-device-loop", action="store_true",
                     help="skip the timing of the step with CG windows under device control")
@@ -542,6 +544,57 @@ def threed_cpu_baseline(nu, nt, window_nodes=32, seconds=8.0):
     return {"value": val, "unit": UNIT, "cores": pool.workers, "kind": "oracle", "sample": desc}
 
 
+def batch_full_time_to_tol(stream, flush, tol=1e-6):
+    """The full 192-system batch (64 shots x 3 frequencies on 256^2/384^2/
+    512^2) solved to a relative FP64 residual of ``tol`` by the batched
+    FP32-stencil / FP64-Krylov solve, measured.  The sequential plain FP64 arm
+    (192 solves, hours) is extrapolated, labelled as such: one representative
+    shot per member (the middle one) solved alone in FP64 to ``tol``,
+    measured, times the member's shot count."""
+    import torch
+    from paper_2205_12344_gb300 import inputs, parallel
+    from paper_2205_12344_gb300.api import WaveHoltz, WaveHoltzBatch
+    members = batch_members()
+    out = {"workload": "64 shots x 3 frequencies on layered 256^2/384^2/512^2, order 4: 192 systems", "tol": tol}
+    with WaveHoltzBatch(members, "fp32") as wb:
+        wb.solve(tol=tol, maxit=2, raise_on_error=False)          # warm: graphs, autotuner
+        torch.cuda.synchronize()
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xs, infos = wb.solve(tol=tol, maxit=200000, raise_on_error=False)
+        e1.record(stream)
+        e1.synchronize()
+        out["batched"] = {"seconds": e0.elapsed_time(e1) / 1e3, "max_iters": max(i.iters for i in infos),
+                          "mean_iters": sum(i.iters for i in infos) / len(infos),
+                          "max_rel_res": max(i.rel_res for i in infos), "status": max(i.status for i in infos)}
+    nu_list, scales = (256, 384, 512), (0.5, 0.75, 1.0)
+    seq, rows = 0.0, []
+    for m, p in enumerate(members):
+        nu = p.n[0] - 2
+        xs_pos = parallel.shot_positions((nu + 1) * 0.01, p.nrhs)
+        q = inputs.cfg_layered_2d(nu=nu, order=4, nrhs=1, shot_x=[xs_pos[p.nrhs // 2]],
+                                  omega_scale=scales[m % len(scales)])
+        with WaveHoltz(q, precision="fp64") as wh:
+            wh.apply_Pi0()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, info = wh.solve(tol=tol, maxit=200000, raise_on_error=False)
+            e1.record(stream)
+            e1.synchronize()
+        s = e0.elapsed_time(e1) / 1e3
+        rows.append({"member": m, "nu": nu, "omega_scale": scales[m % len(scales)], "shots": p.nrhs,
+                     "fp64_seconds_one_shot": s, "fp64_iters": info.iters, "status": info.status})
+        seq += s * p.nrhs
+    out["sequential_fp64_extrapolated"] = {"seconds": seq, "members": rows,
+                                           "how": "one measured FP64 solve per member x its shot count"}
+    out["speedup_batched_vs_sequential_fp64_extrapolated"] = seq / out["batched"]["seconds"]
+    return out
+
+
 def batch_time_to_tol(stream, flush, tol=1e-6):
     """Time to a relative FP64 residual of ``tol`` for a reduced batch (8
     shots x 2 frequencies, 0.5 and 1.0 x w10, on layered 128^2 and 192^2: 16
@@ -783,6 +836,8 @@ def main():
             flush.fill_(1.0)
             extra["batch"] = batch_measurement(args.batch_iters, stream)
             extra["batch"]["time_to_tol"] = batch_time_to_tol(stream, flush)
+            if args.batch_full_tol:
+                extra["batch"]["time_to_tol_full"] = batch_full_time_to_tol(stream, flush)
         if not args.no_mapped:
             extra["mapped"] = mapped_measurement(args.nu, args.mapped_applies, stream, flush)
         if not args.no_3d:
