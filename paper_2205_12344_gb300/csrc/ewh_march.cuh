@@ -80,6 +80,18 @@ __device__ __forceinline__ int zm_hi(int p, int n) {
   return p + 2;
 }
 
+// The last line position p in [lo, cap] whose stencil is complete once
+// position `done` exists, for a segment whose first stencil reaches h0: the
+// largest such p with max(h0, zm_hi(p, n)) <= done (the reach's prefix
+// maximum, non-decreasing in p), or a value below lo when there is none.  In
+// the interior (done in [6, n - 3]) that is done - 2, without the search.
+__device__ __forceinline__ int zm_last_ready(int lo, int cap, int h0, int done, int n) {
+  if (h0 <= done && done >= 6 && done <= n - 3) return min(cap, done - 2);
+  int p = min(cap, done);
+  while (p >= lo && max(h0, zm_hi(p, n)) > done) --p;
+  return p;
+}
+
 __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 __device__ __forceinline__ void st2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
 

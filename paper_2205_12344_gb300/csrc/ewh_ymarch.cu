@@ -232,8 +232,7 @@ __global__ void __launch_bounds__(32) step2d_o4_ym(Geom g, WaveFields<float> f, 
       }
       bool any_sigma = false, failed = false;
       // the last stress row complete at this step (prefix maximum of the reach)
-      int s_last = min(shi, j);
-      while (s_last >= next_s && max(hs0, zm_hi(s_last, n1)) > j) --s_last;
+      const int s_last = zm_last_ready(next_s, shi, hs0, j, n1);
       for (; next_s <= s_last;) {
         const int ys = next_s;
         if (lm_row != ys) {
@@ -336,8 +335,7 @@ __global__ void __launch_bounds__(32) step2d_o4_ym(Geom g, WaveFields<float> f, 
         break;
       }
       // ---- output rows whose stress rows all exist
-      int o_last = min(yb - 1, next_s - 1);
-      while (o_last >= next_o && max(ho0, zm_hi(o_last, n1)) > next_s - 1) --o_last;
+      const int o_last = zm_last_ready(next_o, yb - 1, ho0, next_s - 1, n1);
       for (; next_o <= o_last; ++next_o) {
         const int yo = next_o;
         if (!(ov0 || ov1)) continue;

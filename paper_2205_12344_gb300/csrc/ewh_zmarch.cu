@@ -290,8 +290,7 @@ __global__ void __launch_bounds__(zm_threads<TY>(), TY <= 8 ? 2 : 1)
       // the last stress plane complete at this step: every u plane its prefix of
       // stress planes reads has arrived (the prefix maximum of the reach is
       // max(hs0, hi(zs)), non-decreasing in zs)
-      int s_last = min(shi, j);
-      while (s_last >= next_s && max(hs0, zm_hi(s_last, n2)) > j) --s_last;
+      const int s_last = zm_last_ready(next_s, shi, hs0, j, n2);
       for (; next_s <= s_last;) {
         const int zs = next_s;
         if (lm_plane != zs) {
@@ -439,8 +438,7 @@ __global__ void __launch_bounds__(zm_threads<TY>(), TY <= 8 ? 2 : 1)
         break;
       }
       // ---- output planes whose stress planes all exist
-      int o_last = min(zb - 1, next_s - 1);
-      while (o_last >= next_o && max(ho0, zm_hi(o_last, n2)) > next_s - 1) --o_last;
+      const int o_last = zm_last_ready(next_o, zb - 1, ho0, next_s - 1, n2);
       for (; next_o <= o_last;) {
         const int zo = next_o;
         if (ov0 || ov1) {

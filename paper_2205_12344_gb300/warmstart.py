@@ -271,12 +271,14 @@ def make_media(count, nu, seed0, order=2, ppw=None):
     return probs
 
 
-def solve_all(probs, tol, chunk=16, precision="fp32"):
+def solve_all(probs, tol, chunk=16, precision="fp32", log=None):
     """Solutions with the batched solver (FP64 residual <= tol), and each
     problem's b = Pi 0 and S b (the network's phase inputs)."""
     from .api import WaveHoltzBatch
     sols, bs, sbs = [], [], []
     for i in range(0, len(probs), chunk):
+        if log:
+            log("solutions %d / %d" % (i, len(probs)))
         with WaveHoltzBatch(probs[i:i + chunk], precision) as wb:
             b = wb.apply_Pi0()
             sb = wb.apply_S(b)
@@ -384,12 +386,13 @@ def compare(net, probs, tol, precision="fp32"):
 
 
 def run_experiment(n_train=512, n_test=32, nu=256, epochs=30, batch=8, tol=1e-6, seed=0, log=None, order=2,
-                   ppw=None, lr=1e-3):
-    """Generate solutions, train the network on the GPU, compare solves."""
+                   ppw=None, lr=1e-3, train_tol=None):
+    """Generate solutions (to train_tol, default tol), train the network on
+    the GPU, compare solves to tol with and without the warm start."""
     import time
     t0 = time.perf_counter()
     probs = make_media(n_train + n_test, nu, seed, order=order, ppw=ppw)
-    sols, bs, sbs = solve_all(probs[:n_train], tol)
+    sols, bs, sbs = solve_all(probs[:n_train], train_tol or tol, log=log)
     t_gen = time.perf_counter() - t0
     feats = [features(p, b, sb) for p, b, sb in zip(probs[:n_train], bs, sbs)]
     targs = [target(p, v) for p, v in zip(probs[:n_train], sols)]
@@ -403,6 +406,7 @@ def run_experiment(n_train=512, n_test=32, nu=256, epochs=30, batch=8, tol=1e-6,
     tp = [r["t_plain"] for r in rows]
     tw = [r["t_warm"] for r in rows]
     return {"n_train": n_train, "n_test": n_test, "nu": nu, "epochs": epochs, "tol": tol, "order": order,
+            "train_tol": train_tol or tol,
             "ppw": ppw, "rel_res_b_mean": float(np.mean([r["rel_res_b"] for r in rows])),
             "seconds_generate": t_gen, "seconds_train": t_train, "loss_first": hist[0], "loss_last": hist[-1],
             "iters_plain_mean": float(np.mean(ip)), "iters_warm_mean": float(np.mean(iw)),
@@ -426,12 +430,14 @@ def main(argv=None):
     ap.add_argument("--ppw", type=float, nargs=2, default=None, help="points per wavelength range")
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--train-tol", type=float, default=None, help="residual of the training solutions (default: tol)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=None, help="JSON file for the result")
     a = ap.parse_args(argv)
     import sys
     res = run_experiment(n_train=a.n_train, n_test=a.n_test, nu=a.nu, epochs=a.epochs, batch=a.batch, tol=a.tol,
                          seed=a.seed, order=a.order, ppw=tuple(a.ppw) if a.ppw else None, lr=a.lr,
+                         train_tol=a.train_tol,
                          log=lambda m: print(m, file=sys.stderr, flush=True))
     text = json.dumps(res, indent=1, default=float)
     if a.out:
