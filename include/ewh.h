@@ -199,7 +199,12 @@ ewh_status ewh_mdot(ewh_ctx* ctx, const double* x, const double* y, double* out)
  *   v_out      solution (FP64, host or device), nrhs * n_unknowns.
  *   info       optional; filled on return.
  * Returns EWH_OK, EWH_ENOTCONV (best iterate in v_out), EWH_EBREAKDOWN
- * (indefinite system detected; last iterate in v_out), or an error. */
+ * (indefinite system detected; last iterate in v_out), or an error.
+ * The iterations run under device control: one graph launch runs a window
+ * of up to EWH_CG_POLL (environment, default 32; 1 = the host polls after
+ * every iteration) iterations, a device kernel ending the window when the
+ * host must act (residual replacement, breakdown, iteration limit); the
+ * iterates equal those of the host-polled loop. */
 ewh_status ewh_solve(ewh_ctx* ctx, double tol, int maxit, const double* x0_or_null,
                      double* v_out, ewh_solve_info* info);
 
@@ -302,7 +307,10 @@ ewh_status ewh_batch_apply_S(ewh_batch* b, const double* const* v_in, double* co
 /* Solve every member as ewh_solve does (same tolerance and stopping rule);
  * v_out[k] receives member k's solution (host or device FP64), infos[k] its
  * statistics (optional).  Returns EWH_OK when every member converged, else the
- * first failing member's status (the others are still solved). */
+ * first failing member's status (the others are still solved).  A window of
+ * iterations of every unconverged member is one graph launch (a device-side
+ * loop per member, concurrent; one after another when a member runs the
+ * on-chip solve, whose cooperative launch needs all its CTAs resident). */
 ewh_status ewh_batch_solve(ewh_batch* b, double tol, int maxit, double* const* v_out, ewh_solve_info* infos);
 
 /* The context of member k (owned by the batch; use for ewh_get_info). */
