@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cctype>
 #include <string>
 #include <vector>
 
@@ -352,7 +353,14 @@ std::string tune_key(const ewh_ctx* ctx) {
   for (auto& ch : name)
     if (ch == '"' || ch == ' ') ch = '_';
   const Geom& g = ctx->g;
-  return name + "|v4" + (ctx->batch_member ? "b" : "") + (g.mapped ? "|map" : "") + "|d" + std::to_string(g.dim) +
+  // a batch member whose on-chip plans the batch rule excludes (resident_ok)
+  // has other candidates than the same problem alone
+  bool restricted = false;
+  if (sizeof(T) == 4 && ctx->batch_member)
+    for (int k = 0; k < RS_SHAPES; ++k)
+      restricted = restricted || (ctx->w32.rplan[k].ok && (long long)ctx->w32.rplan[k].bx * ctx->w32.rplan[k].by <
+                                                              RS_BATCH_MIN_BLOCK);
+  return name + "|v4" + (restricted ? "b" : "") + (g.mapped ? "|map" : "") + "|d" + std::to_string(g.dim) +
          "|o" + std::to_string(ctx->order) + "|" +
          (sizeof(T) == 8 ? "f64" : "f32") + "|" + std::to_string(g.n[0]) + "x" + std::to_string(g.n[1]) + "x" +
          std::to_string(g.n[2]) + "|r" + std::to_string(g.nrhs);
@@ -415,7 +423,8 @@ template <typename T>
 void autotune(ewh_ctx* ctx, Wave<T>& w) {
   const int nbase = ctx->g.mapped ? 3 : step_variant_count(ctx->g.dim, ctx->order);
   const char* force = getenv("EWH_STEP2D_O4");
-  const bool forced_launcher = force && (force[0] == 's' || force[0] == 'f' || force[0] == 'y');
+  // a launcher named by the environment (the y-march exists in FP32 only)
+  const bool forced_launcher = force && (force[0] == 's' || force[0] == 'f' || (force[0] == 'y' && sizeof(T) == 4));
   bool any_res = false;
   for (int k = 0; k < RS_SHAPES && !forced_launcher; ++k) any_res |= resident_ok<T>(ctx, w, VARIANT_RESIDENT + k);
   const bool ym = ymarch_ok<T>(ctx, w) && !forced_launcher;
@@ -439,9 +448,15 @@ void autotune(ewh_ctx* ctx, Wave<T>& w) {
     w.variant = 0;
     return;
   }
-  // a choice made under EWH_STEP2D_O4 (a restricted candidate set) is not cached
-  const std::string path = forced_launcher ? std::string() : tune_cache_path();
-  const std::string key = tune_key<T>(ctx);
+  // a choice made under EWH_STEP2D_O4 (a restricted candidate set) is cached
+  // under its own key, so contexts of the same problem make the same choice
+  const std::string path = tune_cache_path();
+  std::string key = tune_key<T>(ctx);
+  if (forced_launcher) {
+    key += "|E";
+    for (const char* c = force; *c; ++c)
+      if (isalnum((unsigned char)*c)) key += *c;  // the cache file quotes keys as they are
+  }
   auto cache = read_tune_cache(path);
   for (auto& kv : cache)
     if (kv.first == key && kv.second >= 0 && kv.second < nv &&
