@@ -262,18 +262,21 @@ ewh_status ewh_get_stats(ewh_ctx* ctx, ewh_stats* out);
 /* Zero the accumulated statistics (the launch counter included). */
 ewh_status ewh_reset_stats(ewh_ctx* ctx);
 
-/* Bound of each grid-barrier wait of the on-chip wave solve (no counterpart in
- * the paper).  The 2D order-4 FP32 single-rhs solve may run every time level in
- * one cooperative launch whose CTAs meet at a grid barrier once per level.
- * Every wait there is bounded: after ns nanoseconds (default 1e9) or 2^22
- * polls the waiting CTA raises an error flag, every CTA leaves at its next
- * barrier, and the launch fills its accumulator with NaN (so ewh_apply_S
- * returns NaN and a solve sees an FP32 breakdown and continues with the FP64
- * operator).  ns = 0 makes every wait give up at once: a way to exercise that
- * path without a hung GPU.  The count of launches that gave up is in
- * ewh_stats.grid_wait_timeouts.  Takes effect for the next launch (the stream
- * is synchronised first); a no-op on contexts that never run on chip.
- * Errors: EWH_EINVAL (ns < 0), EWH_ECUDA. */
+/* Bound of each device-side wait of the FP32 order-4 step kernels (no
+ * counterpart in the paper): the grid barrier of the on-chip wave solve (2D,
+ * every time level in one cooperative launch per group of right-hand sides,
+ * CTAs meeting once per level) and the mbarrier waits of the marching kernels
+ * (2D y-march, 3D z-march) for their bulk-tensor copies.  Every wait is
+ * bounded: after ns nanoseconds (default 1e9; the grid barrier also after 2^22
+ * polls) the waiting CTA gives up (the on-chip solve raises an error flag and
+ * every CTA leaves at its next barrier; a marching CTA waits, bounded, for its
+ * copies in flight and returns), and the launch fills its remaining
+ * accumulator nodes with NaN (so ewh_apply_S returns NaN and a solve sees an
+ * FP32 breakdown and continues with the FP64 operator).  ns = 0 makes every
+ * wait give up at once: a way to exercise that path without a hung GPU.  The
+ * count of give-ups is in ewh_stats.grid_wait_timeouts.  Takes effect for the
+ * next launch (the stream is synchronised first); a no-op on contexts that
+ * run none of these kernels.  Errors: EWH_EINVAL (ns < 0), EWH_ECUDA. */
 ewh_status ewh_set_grid_wait(ewh_ctx* ctx, long long ns);
 
 /* ---- Batches: many independent problems advanced together ----------------

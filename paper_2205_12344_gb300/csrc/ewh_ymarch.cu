@@ -17,9 +17,9 @@
 //     add -D_y sigma_{.y} (+ the y boundary terms) and apply the leapfrog /
 //     filter update (8-byte loads and stores of node pairs).
 // The stresses never leave the chip.  A CTA holds about 13 KB of shared
-// memory, so some 17 CTAs (warps) share an SM, and a launch has one CTA per
-// (right-hand side, strip, row range): the batch members' many right-hand
-// sides fill the GPU.  The rows near the y sides follow the exact reach of
+// memory, so 16 CTAs (warps) share an SM; a persistent grid splits the
+// (right-hand side, strip, row) work into equal contiguous shares of at
+// least EWH_YM_ROWS (32) rows, so many right-hand sides fill the GPU.  The rows near the y sides follow the exact reach of
 // the SBP closure rows (the schedule of ewh_zmarch.cu, along y); the strips'
 // x closures use the per-class tap tables (no lane divergence).  Waits on the
 // mbarriers are bounded by the context's wait limit; a CTA that gives up
