@@ -128,6 +128,8 @@ typedef struct {
                           recomputed with an FP64 S apply */
   double seconds;      /* wall time of the solve (device work included) */
   int status;          /* ewh_status of the solve */
+  int minres_iters;    /* of iters, those of MINRES continuing after CG met
+                          (p, A p)_M <= 0 on the FP64 operator (0 otherwise) */
 } ewh_solve_info;
 
 /* Create a problem (Section 2.1 data, Section 4 discretisation).
@@ -199,8 +201,11 @@ ewh_status ewh_mdot(ewh_ctx* ctx, const double* x, const double* y, double* out)
  *   v_out      solution (FP64, host or device), nrhs * n_unknowns.
  *   info       optional; filled on return.
  * Returns EWH_OK, EWH_ENOTCONV (best iterate in v_out), EWH_EBREAKDOWN
- * (indefinite system detected; last iterate in v_out), or an error.
- * The iterations run under device control: one graph launch runs a window
+ * (last iterate in v_out), or an error.  When CG meets (p, A p)_M <= 0 on
+ * the FP64 operator (M(I - S) indefinite, or numerically so next to a
+ * resonance) the solve continues from the current iterate with MINRES (the
+ * Section 4.4 remark), counted in info.minres_iters; EWH_EBREAKDOWN means
+ * that MINRES broke down too.  The iterations run under device control: one graph launch runs a window
  * of up to EWH_CG_POLL (environment, default 32; 1 = the host polls after
  * every iteration) iterations, a device kernel ending the window when the
  * host must act (residual replacement, breakdown, iteration limit); the

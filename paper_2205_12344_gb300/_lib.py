@@ -31,7 +31,8 @@ class ewh_problem_info(ctypes.Structure):
 
 class ewh_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("s_applies", ctypes.c_int), ("s_applies_fp64", ctypes.c_int),
-                ("rel_res", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+                ("rel_res", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int),
+                ("minres_iters", ctypes.c_int)]
 
 
 class ewh_stats(ctypes.Structure):

@@ -1427,6 +1427,23 @@ ewh_status run_minres(ewh_ctx* ctx, double* x, double* r, double tol, int maxit,
   return EWH_OK;
 }
 
+// CG met (p, A p)_M <= 0 on the FP64 operator: M(I - S) is indefinite, or
+// numerically so next to a resonance.  Continue from the current iterate with
+// MINRES (the remark of Section 4.4 on indefinite systems), restarted from the
+// true FP64 residual; its iterations are counted in inf->minres_iters.
+// *result becomes MINRES's status.
+ewh_status minres_after_breakdown(ewh_ctx* ctx, double tol, int maxit, ewh_solve_info* inf, double* rel,
+                                  ewh_status* result) {
+  ewh_status s = true_residual(ctx, ctx->kx, ctx->kr, rel);
+  if (s != EWH_OK) return s;
+  ++inf->s_applies_fp64;
+  ctx->err = "no error";
+  const int it0 = inf->iters;
+  *result = run_minres<double>(ctx, ctx->kx, ctx->kr, tol, maxit, 0.0, inf, rel);
+  inf->minres_iters += inf->iters - it0;
+  return EWH_OK;
+}
+
 ewh_status solve_impl(ewh_ctx* ctx, double tol, int maxit, const double* x0, double* v_out,
                       ewh_solve_info* inf, int method = 0) {
   const Geom& g = ctx->g;
@@ -1481,6 +1498,10 @@ ewh_status solve_impl(ewh_ctx* ctx, double tol, int maxit, const double* x0, dou
       ctx->err = "no error";
       result = run_cg<double>(ctx, ctx->kx, ctx->kr, tol, maxit, 0.0, inf, &rel);
     }
+  }
+  if (result == EWH_EBREAKDOWN && method != 2) {  // CG or CR met an indefinite system
+    s = minres_after_breakdown(ctx, tol, maxit, inf, &rel, &result);
+    if (s != EWH_OK) return s;
   }
   if (result != EWH_OK && result != EWH_EBREAKDOWN) return result;
   inf->rel_res = rel;
@@ -1785,7 +1806,7 @@ ewh_status batch_solve_T(ewh_batch* b, double tol, int maxit, double* const* v_o
     members.swap(next);
   }
   // members whose FP32 operator lost definiteness continue alone in FP64;
-  // FP64 members that broke down report it
+  // members whose FP64 CG broke down continue with MINRES (as ewh_solve)
   for (int k = 0; k < P; ++k) {
     ewh_ctx* ctx = b->p[k];
     double rel = cg_worst_true(cs[k]);
@@ -1798,6 +1819,10 @@ ewh_status batch_solve_T(ewh_batch* b, double tol, int maxit, double* const* v_o
         status[k] = run_cg<double>(ctx, ctx->kx, ctx->kr, tol, maxit, 0.0, &inf[k], &rel);
       } else {
         status[k] = EWH_EBREAKDOWN;
+      }
+      if (status[k] == EWH_EBREAKDOWN) {
+        ewh_status s = minres_after_breakdown(ctx, tol, maxit, &inf[k], &rel, &status[k]);
+        if (s != EWH_OK) return bfail(b, s, ctx->err);
       }
     }
     inf[k].rel_res = rel;

@@ -359,3 +359,18 @@ def test_minres_solves_indefinite_system():
     assert info.status == 0 and info.rel_res <= 1e-11
     assert np.all(np.diff(hist) <= 1e-12)
     assert np.linalg.norm(to_np(x) - v) <= 1e-8 * np.linalg.norm(v)
+
+
+def test_cg_continues_with_minres_on_indefinite_system():
+    """CG on the same indefinite system meets (p, A p)_M <= 0 (at its 26th
+    iteration in the oracle's arithmetic); ewh_solve continues from that
+    iterate with MINRES (Section 4.4 remark) and reaches the discrete
+    Helmholtz solution, counting the MINRES iterations apart."""
+    p = inputs.small_problem(2, [6, 5], 2, [0, 1, 0, 0], seed=3, omega=24.75)
+    s = O.build_system(p, nt=5)
+    v = O.helmholtz_direct(s)
+    with _wh(p, nt=5) as wh:
+        x, info = wh.solve(tol=1e-11, maxit=500)
+    assert info.status == 0 and info.rel_res <= 1e-11
+    assert 0 < info.minres_iters < info.iters
+    assert np.linalg.norm(to_np(x) - v) <= 1e-8 * np.linalg.norm(v)
