@@ -143,3 +143,36 @@ def test_mapped_create_without_device_reports_ecuda(lib):
     s, out = _call_create_mapped(lib, _desc(order=4, n=[10, 12, 1]), Q, R, m)
     assert s == _lib.EWH_ECUDA
     assert not out.value
+
+
+def test_ctypes_structures_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets of
+    the header's C struct (compiled with the host compiler): a field added on
+    one side only would shift the others silently."""
+    import shutil
+    import subprocess
+    from paper_2205_12344_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"ewh_grid_desc": _lib.ewh_grid_desc, "ewh_problem_info": _lib.ewh_problem_info,
+               "ewh_solve_info": _lib.ewh_solve_info, "ewh_stats": _lib.ewh_stats, "ewh_problem": _lib.ewh_problem}
+    c_name = {"lambda_": "lambda"}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ewh.h"', "int main(void) {"]
+    for s, cls in structs.items():
+        lines.append('  printf("%s %%zu\\n", sizeof(%s));' % (s, s))
+        for f, _ in cls._fields_:
+            cf = c_name.get(f, f)
+            lines.append('  printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (s, f, s, cf))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                   check=True).stdout.splitlines())
+    for s, cls in structs.items():
+        assert int(got[s]) == ctypes.sizeof(cls), s
+        for f, _ in cls._fields_:
+            assert int(got["%s.%s" % (s, f)]) == getattr(cls, f).offset, (s, f)
