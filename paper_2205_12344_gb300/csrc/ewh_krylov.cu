@@ -42,51 +42,49 @@ __device__ __forceinline__ void node_coords(const Geom& g, long long node, int& 
   z += g.off[2];
 }
 
+// The dense unknown layout [rhs][comp][z][y][x] walked by rows: block b takes
+// rows b, b + gridDim.x, ... (row = ((rhs dim + comp) nu2 + z) nu1 + y), its
+// threads the x of a row, so the index arithmetic is a few divisions per row
+// and both the dense and the padded accesses are coalesced.  body(i, o, rhs):
+// dense index i, padded offset o.
+template <typename F>
+__device__ __forceinline__ void for_dense_rows(const Geom& g, F body) {
+  const int nu0 = g.nu[0], nu1 = g.nu[1], nu2 = g.nu[2];
+  const long long nrows = (long long)g.nrhs * g.dim * nu2 * nu1;
+  for (long long row = blockIdx.x; row < nrows; row += gridDim.x) {
+    const int y = (int)(row % nu1);
+    long long t = row / nu1;
+    const int z = (int)(t % nu2);
+    t /= nu2;
+    const int comp = (int)(t % g.dim), rhs = (int)(t / g.dim);
+    const long long i0 = row * nu0;
+    const long long o0 = pidx(g, rhs, comp, g.off[0], y + g.off[1], z + g.off[2]);
+    for (int x = threadIdx.x; x < nu0; x += blockDim.x) body(i0 + x, o0 + x, rhs);
+  }
+}
+
 template <typename T>
 __global__ void pack_kernel(Geom g, const double* __restrict__ dense, T* __restrict__ padded) {
-  const long long total = (long long)g.nrhs * g.dim * g.nodes;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long node = i % g.nodes;
-    const long long rc = i / g.nodes;
-    const int comp = (int)(rc % g.dim), rhs = (int)(rc / g.dim);
-    int x, y, z;
-    node_coords(g, node, x, y, z);
-    padded[pidx(g, rhs, comp, x, y, z)] = (T)dense[i];
-  }
+  for_dense_rows(g, [&](long long i, long long o, int) { padded[o] = (T)dense[i]; });
 }
 
 template <typename T>
 __global__ void unpack_kernel(Geom g, const T* __restrict__ padded, double* __restrict__ dense,
                               const double* __restrict__ sub_from) {
-  const long long total = (long long)g.nrhs * g.dim * g.nodes;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long node = i % g.nodes;
-    const long long rc = i / g.nodes;
-    const int comp = (int)(rc % g.dim), rhs = (int)(rc / g.dim);
-    int x, y, z;
-    node_coords(g, node, x, y, z);
-    const double v = (double)padded[pidx(g, rhs, comp, x, y, z)];
+  for_dense_rows(g, [&](long long i, long long o, int) {
+    const double v = (double)padded[o];
     dense[i] = sub_from ? sub_from[i] - v : v;
-  }
+  });
 }
 
 template <typename T>
 __global__ void pupdate_pack_kernel(Geom g, const double* __restrict__ r, double* __restrict__ p,
                                     const double* __restrict__ beta, T* __restrict__ padded) {
-  const long long total = (long long)g.nrhs * g.dim * g.nodes;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long node = i % g.nodes;
-    const long long rc = i / g.nodes;
-    const int comp = (int)(rc % g.dim), rhs = (int)(rc / g.dim);
+  for_dense_rows(g, [&](long long i, long long o, int rhs) {
     const double pn = r[i] + beta[rhs] * p[i];
     p[i] = pn;
-    int x, y, z;
-    node_coords(g, node, x, y, z);
-    padded[pidx(g, rhs, comp, x, y, z)] = (T)pn;
-  }
+    padded[o] = (T)pn;
+  });
 }
 
 static int grid_for(long long n) {
@@ -96,24 +94,33 @@ static int grid_for(long long n) {
   return (int)b;
 }
 
+// launch shape of the row walks: one block per row (up to 16 per SM), a
+// warp-multiple of threads up to 256
+static dim3 rows_grid(const Geom& g) {
+  long long rows = (long long)g.nrhs * g.dim * g.nu[2] * g.nu[1];
+  if (rows > 152 * 16) rows = 152 * 16;
+  return dim3((unsigned)(rows < 1 ? 1 : rows));
+}
+static dim3 rows_block(const Geom& g) {
+  const int t = ((g.nu[0] + 31) / 32) * 32;
+  return dim3(t > 256 ? 256 : t);
+}
+
 template <typename T>
 cudaError_t launch_pack(const Geom& g, const double* dense, T* padded, cudaStream_t st) {
-  const long long n = (long long)g.nrhs * g.dim * g.nodes;
-  pack_kernel<T><<<grid_for(n), 256, 0, st>>>(g, dense, padded);
+  pack_kernel<T><<<rows_grid(g), rows_block(g), 0, st>>>(g, dense, padded);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_unpack(const Geom& g, const T* padded, double* dense, const double* sub_from,
                           cudaStream_t st) {
-  const long long n = (long long)g.nrhs * g.dim * g.nodes;
-  unpack_kernel<T><<<grid_for(n), 256, 0, st>>>(g, padded, dense, sub_from);
+  unpack_kernel<T><<<rows_grid(g), rows_block(g), 0, st>>>(g, padded, dense, sub_from);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_pupdate_pack(const Geom& g, const double* r, double* p, const double* beta, T* padded,
                                 cudaStream_t st) {
-  const long long n = (long long)g.nrhs * g.dim * g.nodes;
-  pupdate_pack_kernel<T><<<grid_for(n), 256, 0, st>>>(g, r, p, beta, padded);
+  pupdate_pack_kernel<T><<<rows_grid(g), rows_block(g), 0, st>>>(g, r, p, beta, padded);
   return cudaGetLastError();
 }
 
@@ -131,12 +138,14 @@ __global__ void mdot_partial_kernel(Geom g, const double* __restrict__ mw, const
                                     const double* __restrict__ y, double* __restrict__ part) {
   const int rhs = blockIdx.y;
   const long long n = (long long)g.dim * g.nodes;
-  const double* xr = x + (long long)rhs * n;
-  const double* yr = y + (long long)rhs * n;
   double s = 0.0;
-  for (long long i = blockIdx.x * (long long)RED_THREADS + threadIdx.x; i < n;
-       i += (long long)gridDim.x * RED_THREADS)
-    s += mw[i % g.nodes] * xr[i] * yr[i];
+  for (int c = 0; c < g.dim; ++c) {  // per component: the weight index is the node index
+    const double* xr = x + (long long)rhs * n + (long long)c * g.nodes;
+    const double* yr = y + (long long)rhs * n + (long long)c * g.nodes;
+    for (long long j = blockIdx.x * (long long)RED_THREADS + threadIdx.x; j < g.nodes;
+         j += (long long)gridDim.x * RED_THREADS)
+      s += mw[j] * xr[j] * yr[j];
+  }
   s = block_sum(s);
   if (threadIdx.x == 0) part[(long long)rhs * gridDim.x + blockIdx.x] = s;
 }
@@ -189,16 +198,18 @@ __global__ void cg_xr_kernel(Geom g, const double* __restrict__ mw, const double
                              double* __restrict__ r, double* __restrict__ part) {
   const int rhs = blockIdx.y;
   const long long n = (long long)g.dim * g.nodes;
-  const long long base = (long long)rhs * n;
   const double a = alpha[rhs];
   double s = 0.0;
-  for (long long i = blockIdx.x * (long long)RED_THREADS + threadIdx.x; i < n;
-       i += (long long)gridDim.x * RED_THREADS) {
-    const long long k = base + i;
-    x[k] += a * p[k];
-    const double rn = r[k] - a * q[k];
-    r[k] = rn;
-    s += mw[i % g.nodes] * rn * rn;
+  for (int c = 0; c < g.dim; ++c) {  // per component: the weight index is the node index
+    const long long base = (long long)rhs * n + (long long)c * g.nodes;
+    for (long long j = blockIdx.x * (long long)RED_THREADS + threadIdx.x; j < g.nodes;
+         j += (long long)gridDim.x * RED_THREADS) {
+      const long long k = base + j;
+      x[k] += a * p[k];
+      const double rn = r[k] - a * q[k];
+      r[k] = rn;
+      s += mw[j] * rn * rn;
+    }
   }
   s = block_sum(s);
   if (threadIdx.x == 0) part[(long long)rhs * gridDim.x + blockIdx.x] = s;
