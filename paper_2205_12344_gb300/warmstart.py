@@ -11,9 +11,9 @@ kernels; PyTorch only provides device memory and the stream.
 
 Use: x0 = c1 y + c2 b with (c1, c2) minimising ||b - A x0||_M (A = I - S;
 A b = b - S b is known, A y costs one S apply), which never raises the
-initial residual above ||b||_M: the plain solve stays the fallback and the
-judge of the result (the solve's stopping rule is the FP64 residual,
-whatever the start).
+initial residual above ||b||_M: the plain solve stays the fallback, and the
+solve's stopping rule (the FP64 residual) decides the result whatever the
+start.
 """
 from __future__ import annotations
 

@@ -2,7 +2,8 @@
 generated by the solver itself, the network trained on the GPU by the
 library's forward/backward kernels, and the with/without comparison on
 held-out media.  The network's output has no exact pin: the FP64 residual of
-the solve judges it (the scaled start never raises the initial residual)."""
+the solve decides whether it is good enough (the least-squares start never
+raises the initial residual)."""
 import math
 
 import numpy as np
